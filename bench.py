@@ -1,0 +1,447 @@
+#!/usr/bin/env python3
+"""Throughput of the FX correlator on the paper's real-time workload.
+
+Workload (Sec. 1 of the paper: 44 elements, 4-bit, 512-point FFT, sampling
+rate restricted to ~35 MS/s): N = 44 antennas, K = 512, one step = one 1 s
+integration at 35 MS/s = 68359 whole spectra per antenna (35e6 // 512),
+pushed through the C ABI in 2^20-sample chunks (33 x 2048 spectra + 775),
+then dumped to a device buffer.  Input: seeded synthetic 4-bit data (N(0, 2)
+noise + 1% correlated component + a 0.5 LSB tone at channel 97), 770 MB per
+step resident in HBM -- larger than the 126 MB L2, so no flush is needed.
+
+value       antenna-samples/s over the timed steps (whole job);
+rtf         real-time factor = value / (N * 35e6);
+e2e         same metric through the C ABI from pinned host memory, H2D of each
+            step's input and D2H of its visibilities inside the timed region;
+roofline    dominant kernel: algorithmic work per launch / its CUDA-event time;
+cpu_baseline the FP64 oracle on the host cores, on a bounded sample.
+
+``--impl reference`` times the oracle itself (the only reference this method
+has) on the same metric, one bounded sample of the workload per step.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "antenna-samples/s & real-time factor (44 el, 35 MS/s); TC vs FP32 at stated error"
+UNIT = "antenna-samples/s"
+N_ANT, K_FFT, RATE = 44, 512, 35e6
+SPEC_PER_STEP = int(RATE // K_FFT)            # 68359 whole spectra in 1 s
+CHUNK_FRAMES = (1 << 20) // K_FFT             # 2048 spectra per push
+SEED = 11020148 + 2
+# The paper's cluster handles the real-time rate of this workload:
+# 770e6 B/s of 4-bit samples = 1.54e9 antenna-samples/s (Sec. 1, abstract).
+PAPER_RATE = N_ANT * RATE
+
+WORKLOAD = ("N=44 antennas, K=512-point real FFT -> 256 channels, 990 outputs/channel, "
+            "35 MS/s, 1 s integration = 68359 spectra per step in 2^20-sample pushes")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="fp32", choices=["fp32", "fp16", "fp8", "fp32_simt"])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(gpu_id)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        self.t0 = time.time()
+
+    def stop(self):
+        self.t1 = time.time()
+
+    def result(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = []
+        for line in self.f.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                ts += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+            except (ValueError, IndexError):
+                continue
+        os.unlink(self.f.name)
+        inside = [r for r in rows if self.t0 - 0.15 <= r[0] <= self.t1 + 0.15]
+        use = inside if inside else rows
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in use for i, v in enumerate(r[3]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[1] for r in use),
+                "sm_max_mhz": max(r[2] for r in use), "reasons": reasons,
+                "samples": len(use), "in_region": bool(inside)}
+
+
+def gpu_id_for_smi(local_rank):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(local_rank).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[local_rank] if vis else str(local_rank)
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline key)
+# ----------------------------------------------------------------------------
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return max(n)
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def oracle_input(frames, seed=SEED):
+    from paper_1102_0148_gb300 import synth
+    packed, _ = synth.make_samples(N_ANT, frames * K_FFT, K_FFT, seed=seed, tone_amp=0.5)
+    return packed
+
+
+def time_oracle(packed):
+    import oracle
+    frames = packed.shape[0]
+    t0 = time.perf_counter()
+    V, n = oracle.correlate(packed, N_ANT, K_FFT)
+    dt = time.perf_counter() - t0
+    assert n == frames and V.shape == (990, 256)
+    return dt
+
+
+def oracle_frames_for(seconds):
+    """Frames the oracle processes in about `seconds` (probe + proportional)."""
+    probe = 1024
+    dt = time_oracle(oracle_input(probe))
+    frames = int(probe * seconds / max(dt, 1e-3))
+    return max(16, min(SPEC_PER_STEP, frames))
+
+
+def cpu_baseline(seconds):
+    frames = oracle_frames_for(seconds)
+    dt = time_oracle(oracle_input(frames))
+    return {"value": N_ANT * frames * K_FFT / dt, "unit": UNIT, "cores": blas_threads(),
+            "kind": "oracle",
+            "sample": f"first {frames} of the 68359 spectra of one 1 s integration "
+                      f"({frames * K_FFT} samples x 44 antennas), numpy FP64 oracle, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return 0
+    budget = 90.0 / max(1, args.steps + args.warmup)
+    frames = oracle_frames_for(budget)
+    packed = oracle_input(frames)
+    for _ in range(args.warmup):
+        time_oracle(packed)
+    times = [time_oracle(packed) for _ in range(args.steps)]
+    total = sum(times)
+    value = N_ANT * frames * K_FFT * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": value / PAPER_RATE, "dtype": "f64",
+        "data": "synthetic", "rtf": value / PAPER_RATE,
+        "config": {"workload": WORKLOAD, "sample_spectra_per_step": frames},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                         "sample": f"{frames} spectra x 44 antennas per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    rank, local_rank, world = env_rank()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_1102_0148_gb300 import corr, synth, workload
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    peak_src = "measured" if peaks else "fallback"
+
+    dtype = corr.DTYPES[args.dtype]
+    frames = SPEC_PER_STEP
+    rec = N_ANT * K_FFT // 2
+    dev_in, info = synth.make_samples_torch(N_ANT, frames * K_FFT, K_FFT, seed=SEED + rank,
+                                            device="cuda", tone_amp=0.5)
+    dev_in = dev_in.reshape(-1)
+    stream = torch.cuda.current_stream()
+    h = corr.corr_create(N_ANT, K_FFT, dtype)
+    corr.corr_set_stream(h, stream.cuda_stream)
+    info_h = corr.corr_info(h)
+    P, C = info_h["P"], info_h["C"]
+    vis = torch.empty((P, C), dtype=torch.complex64, device="cuda")
+    base = dev_in.data_ptr()
+    pushes = [(f0, min(CHUNK_FRAMES, frames - f0)) for f0 in range(0, frames, CHUNK_FRAMES)]
+
+    def step(src_base):
+        for f0, nf in pushes:
+            corr.corr_push(h, src_base + f0 * rec, nf * K_FFT)
+        return corr.corr_dump(h, vis)
+
+    for _ in range(args.warmup):
+        assert step(base) == frames
+    torch.cuda.synchronize()
+    corr.corr_profile_enable(h, True)
+    corr.corr_profile_read(h)
+
+    sampler = ClockSampler(gpu_id_for_smi(local_rank))
+    time.sleep(1.0)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    sampler.start()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(base)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sampler.stop()
+    if dist:
+        dist.barrier()
+    t = ev0.elapsed_time(ev1) / 1e3
+    if dist:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    clocks = sampler.result()
+    prof = corr.corr_profile_read(h)
+    corr.corr_profile_enable(h, False)
+    launches = sum(v[0] for v in prof.values())
+
+    samples_total = world * N_ANT * frames * K_FFT * args.steps
+    value = samples_total / t
+
+    # roofline of the dominant kernel (largest summed event time)
+    spec_total = frames * args.steps
+    dom = max(("fengine", "xengine"), key=lambda c: prof[c][1])
+    n_launch, ms = prof[dom]
+    if dom == "xengine":
+        work = workload.xengine_flops(N_ANT, K_FFT, spec_total) / n_launch
+        if args.dtype == "fp32_simt":
+            bound, unit = "alu", "TFLOP/s"
+            peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+            psrc = f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"
+        else:
+            bound, unit = "tensor", "TFLOP/s"
+            ratio = {"fp32": 1.1 / 2.25, "fp16": 1.0, "fp8": 2.0}[args.dtype]
+            peak = bf16_peak * ratio
+            psrc = (f"{peak_src} bf16 {bf16_peak} TF/s x nominal "
+                    f"{ {'fp32': 'tf32/bf16 = 1.1/2.25', 'fp16': '1', 'fp8': 'fp8/bf16 = 2'}[args.dtype] }")
+        achieved = work / (ms / n_launch / 1e3) / 1e12
+    else:
+        ob = {"fp32": 4, "fp32_simt": 4, "fp16": 2, "fp8": 1}[args.dtype]
+        work = workload.fengine_bytes(N_ANT, K_FFT, spec_total, ob) / n_launch
+        bound, unit = "hbm", "GB/s"
+        peak = hbm_peak
+        psrc = f"{peak_src} hbm_gbs"
+        achieved = work / (ms / n_launch / 1e3) / 1e9
+    roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "peak_source": psrc,
+                "work_per_launch": work,
+                "kernel_ms": {c: prof[c][1] for c in prof},
+                "kernel_launches": {c: prof[c][0] for c in prof}}
+
+    # end to end from pinned host memory through the C ABI
+    e2e = None
+    if args.e2e_steps > 0:
+        host_in = torch.empty(dev_in.numel(), dtype=torch.uint8, pin_memory=True)
+        host_in.copy_(dev_in)
+        host_vis = np.empty((P, C), np.complex64)
+        hb = host_in.data_ptr()
+
+        def step_host():
+            for f0, nf in pushes:
+                corr.corr_push(h, hb + f0 * rec, nf * K_FFT)
+            return corr.corr_dump(h, host_vis)
+
+        step_host()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            step_host()
+        te = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": world * N_ANT * frames * K_FFT * args.e2e_steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": frames * rec, "d2h_bytes_per_step": host_vis.nbytes,
+               "steps": args.e2e_steps}
+        del host_in
+
+    # TC vs FP32: the other X-engine precisions on the same integration
+    variants = None
+    if not args.no_variants and rank == 0:
+        variants = measure_variants(corr, torch, np, dev_in, pushes, rec, args.dtype)
+
+    corr.corr_destroy(h)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_RATE,
+            "dtype": "f32" if args.dtype.startswith("fp32") else args.dtype,
+            "data": "synthetic",
+            "rtf": value / (world * N_ANT * RATE),
+            "config": {"workload": WORKLOAD, "x_engine": args.dtype,
+                       "spectra_per_step": frames, "chunk_samples": CHUNK_FRAMES * K_FFT,
+                       "input_bytes_per_step": frames * rec,
+                       "l2": "inputs (770 MB/step) larger than L2; no flush",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clocks, "gpu_launches": launches, "roofline": roofline,
+            "e2e": e2e, "cpu_baseline": cpu, "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_variants(corr, torch, np, dev_in, pushes, rec, main_dtype, steps=20):
+    """Throughput of each X-engine precision and its normalised visibility
+    error against the FP32 tensor-core path on the same 1 s integration."""
+    out = {}
+    ref = None
+    order = ["fp32", "fp32_simt", "fp16", "fp8"]
+    res = {}
+    for name in order:
+        try:
+            h = corr.corr_create(N_ANT, K_FFT, corr.DTYPES[name])
+        except corr.CorrError as e:
+            out[name] = {"unavailable": str(e)}
+            continue
+        stream = torch.cuda.current_stream()
+        corr.corr_set_stream(h, stream.cuda_stream)
+        vis = torch.empty((990, 256), dtype=torch.complex128, device="cuda")
+        base = dev_in.data_ptr()
+
+        def step():
+            for f0, nf in pushes:
+                corr.corr_push(h, base + f0 * rec, nf * K_FFT)
+            return corr.corr_dump(h, vis, fp64=True)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1) / 1e3
+        V = vis.cpu().numpy()
+        corr.corr_destroy(h)
+        res[name] = V
+        val = N_ANT * SPEC_PER_STEP * K_FFT * steps / t
+        out[name] = {"value": val, "rtf": val / (N_ANT * RATE)}
+    ref = res.get("fp32")
+    if ref is not None:
+        autos = [i * N_ANT - i * (i - 1) // 2 for i in range(N_ANT)]
+        A = np.abs(ref[autos])
+        ii = [i for i in range(N_ANT) for j in range(i, N_ANT)]
+        jj = [j for i in range(N_ANT) for j in range(i, N_ANT)]
+        nrm = np.sqrt(A[ii] * A[jj])
+        for name, V in res.items():
+            out[name]["err_vs_fp32"] = float(np.max(np.abs(V - ref) / nrm))
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

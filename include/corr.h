@@ -1,0 +1,164 @@
+/*
+ * corr.h -- C ABI of gbcorr, an FX spectral correlator for one GB300 GPU.
+ *
+ * The method is the software spectral correlator of Prasad & Subrahmanya
+ * ("Software Spectral Correlator for the 44-Element Ooty Radio Telescope"):
+ * every antenna's real sample stream is transformed to spectral channels by
+ * an FFT (the F-engine), and for every channel every pair of antennas is
+ * cross-multiplied and accumulated to the required cadence (the X-engine),
+ * giving the cross power spectra (Sec. 1 of the paper).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  N       antennas (elements), 1 <= N <= CORR_MAX_N.
+ *  K       transform length in real samples, a power of two in [16, 4096];
+ *          the paper uses K = 512 (Sec. 4).
+ *  C       = K/2 channels, k = 0 .. K/2-1: DC kept, the Nyquist bin dropped
+ *          (Sec. 1: K channels per 2K-point transform).
+ *  P       = N(N+1)/2 outputs per channel: every pair i <= j including the
+ *          autocorrelations, in row-major upper-triangle order,
+ *          p(i, j) = i*N - i*(i-1)/2 + (j - i).
+ *
+ *  Input samples: 4-bit two's-complement integers in [-8, 7], two per byte,
+ *  the earlier sample in the low nibble (Sec. 1: 4-bit quantisation).  Bytes
+ *  are grouped in frames of K samples of *every* antenna (Sec. 2.2: a frame
+ *  holds contiguous samples from all elements): layout
+ *  [n/K frames][N antennas][K/2 bytes], frame-major.
+ *
+ *  Transform: X_i[s,k] = sum_{n<K} x_i[s*K+n] exp(-2 pi i k n / K), forward
+ *  and unnormalised (Sec. 4).  Optional correction (Sec. 2.1):
+ *  Y_i[s,k] = g_i exp(-2 pi i k tau_i / K) X_i[s,k] -- a complex gain g_i and
+ *  a delay tau_i (samples, any real value) applied to antenna i.
+ *
+ *  Output: V_ij[k] = sum_s Y_i[s,k] conj(Y_j[s,k]), the raw sum over the
+ *  n_spec spectra pushed since the last dump (divide by n_spec for a mean),
+ *  laid out [P][C] as interleaved complex (re, im).
+ *
+ * Memory, streams and errors
+ * --------------------------
+ *  Pointers may be host or device memory unless stated otherwise; the
+ *  library detects which.  The caller owns every buffer it passes; the handle
+ *  owns its workspaces.  Work is queued on the handle's stream (its own
+ *  non-blocking stream unless corr_set_stream gave another).  corr_push
+ *  returns once its work is queued; a device input buffer must stay valid
+ *  until the next corr_dump or corr_sync.  Every call returns CORR_OK or a
+ *  negative corr_status; on error the accumulated state is unchanged unless
+ *  stated, and corr_last_error(h) returns a one-line message (for errors of
+ *  corr_create, call corr_last_error(NULL) on the same thread).  One handle
+ *  must not be used from two host threads at once.
+ */
+#ifndef GBCORR_CORR_H
+#define GBCORR_CORR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CORR_MAX_N 512
+
+typedef struct corr_s* corr_t;
+
+/* X-engine input precision. */
+enum corr_dtype {
+    /* FP32-accurate: the F-engine writes FP32 spectra; the X-engine runs on
+       the tensor cores with each operand split into two TF32 terms. */
+    CORR_FP32 = 0,
+    /* Spectra scaled per (antenna, channel) and cast to FP16 / FP8-E4M3 before
+       the tensor-core X-engine; FP32 accumulation; descaled at the flush.
+       This is the paper's float-to-short-complex conversion with prescaling
+       (Sec. 4) moved to tensor-core types. */
+    CORR_FP16 = 1,
+    CORR_FP8E4M3 = 2,
+    /* FP32 spectra and an FP32 X-engine on the CUDA cores (no tensor cores). */
+    CORR_FP32_SIMT = 3
+};
+
+enum corr_status {
+    CORR_OK = 0,
+    CORR_EINVAL = -1,    /* bad argument or size                          */
+    CORR_ENOMEM = -2,    /* device or host allocation failed              */
+    CORR_ECUDA = -3,     /* a CUDA call failed (message has the CUDA error) */
+    CORR_ETIMEOUT = -4,  /* a bounded device-side wait gave up            */
+    CORR_ESTATE = -5,    /* call not valid in the handle's current state  */
+    CORR_EUNSUPPORTED = -6 /* valid request this build cannot serve       */
+};
+
+/* Create a correlator for N antennas, K-point transforms and X-engine
+ * precision dtype.  Allocates the workspaces on the current CUDA device.
+ * *out is set to NULL on failure. */
+int corr_create(corr_t* out, int N, int K, int dtype);
+
+/* Queue later work on `stream` (a cudaStream_t of the handle's device; NULL
+ * means the legacy default stream).  Waits for the handle's queued work
+ * first. */
+int corr_set_stream(corr_t h, void* stream);
+
+/* Largest number of spectra processed per internal pass (the spectra
+ * workspace holds this many frames).  Rounded up to a multiple of 128;
+ * default 2048.  Reallocates the workspace; only valid with nothing pushed
+ * since the last dump. */
+int corr_set_chunk(corr_t h, int64_t max_spectra);
+
+/* Per-antenna corrections of Sec. 2.1.  gains: N complex values as 2N floats
+ * (re, im); delays: N floats, in samples.  Either may be NULL (gain 1,
+ * delay 0); both NULL switches corrections off.  Host or device memory; the
+ * values are copied before return.  Takes effect for spectra pushed later. */
+int corr_set_corrections(corr_t h, const float* gains, const float* delays);
+
+/* Correlate n samples per antenna (n a multiple of K, n >= 0) and add them
+ * to the running integration.  `samples` holds n/K frames in the layout
+ * above (n*N/2 bytes).  Host memory is staged through the handle's pinned
+ * buffers; device memory is read in place. */
+int corr_push(corr_t h, const uint8_t* samples, int64_t n);
+
+/* Finish the integration: write V to `vis` ([P][C] complex64, or complex128
+ * when vis_fp64 != 0), store the number of spectra summed in *n_spec (may be
+ * NULL), and reset the accumulators.  Synchronises the handle's stream.
+ * Accumulation across pushes is in FP64 on the device. */
+int corr_dump(corr_t h, void* vis, int64_t* n_spec, int vis_fp64);
+
+/* Wait for the handle's queued work; reports device-side errors. */
+int corr_sync(corr_t h);
+
+/* Release everything the handle owns.  NULL is a no-op. */
+void corr_destroy(corr_t h);
+
+/* Message of the last failed call on h (or of this thread's last failed
+ * corr_create when h is NULL).  Never NULL; valid until the next call. */
+const char* corr_last_error(corr_t h);
+
+/* Sizes of a handle: any pointer may be NULL. */
+int corr_info(corr_t h, int* N, int* K, int* C, int* P, int* dtype);
+
+/* Kernel classes reported by corr_profile_read. */
+enum corr_kernel {
+    CORR_KERNEL_FENGINE = 0, /* unpack + correction + FFT + corner turn    */
+    CORR_KERNEL_XENGINE = 1, /* cross-multiply-accumulate                  */
+    CORR_KERNEL_REDUCE = 2,  /* FP64 accumulation of the X-engine partials */
+    CORR_KERNEL_DUMP = 3,    /* accumulator -> [P][C] output               */
+    CORR_KERNEL_COUNT = 4
+};
+
+/* Instrumentation (no counterpart in the paper): while enabled, every kernel
+ * the handle launches is bracketed by a pair of CUDA events on the stream it
+ * is launched on.  corr_profile_read waits for the handle's stream, writes
+ * for each class c < n the number of launches (launches[c]) and their summed
+ * event-to-event time in milliseconds (ms[c]) since the last read, and
+ * clears the counters.  Either output may be NULL. */
+int corr_profile_enable(corr_t h, int on);
+int corr_profile_read(corr_t h, int64_t* launches, double* ms, int n);
+
+/* F-engine only, for inspection: transform n samples per antenna (after
+ * the handle's corrections) and write the spectra Y to `spectra` as
+ * [N][n/K][C] complex64 (device memory).  Leaves the integration untouched;
+ * n/K must not exceed the chunk size.  Synchronises the handle's stream. */
+int corr_debug_spectra(corr_t h, const uint8_t* samples, int64_t n, float* spectra);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBCORR_CORR_H */

@@ -1,0 +1,209 @@
+"""Thin ctypes binding of the C ABI in ``include/corr.h`` (same names).
+
+Argument marshalling only: every step of the correlator runs in the CUDA
+kernels of ``libgbcorr.so``.  Buffers may be torch tensors (device or host),
+numpy arrays (host) or raw integer addresses.  Importing this module loads
+the library and raises ``ImportError`` if it has not been built -- there is
+no fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB_PATH
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -m paper_1102_0148_gb300.build` "
+        "(or __graft_entry__.build()); gbcorr has no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+CORR_FP32, CORR_FP16, CORR_FP8E4M3, CORR_FP32_SIMT = 0, 1, 2, 3
+CORR_OK, CORR_EINVAL, CORR_ENOMEM, CORR_ECUDA, CORR_ETIMEOUT, CORR_ESTATE, CORR_EUNSUPPORTED = (
+    0, -1, -2, -3, -4, -5, -6)
+CORR_MAX_N = 512
+KERNEL_CLASSES = ("fengine", "xengine", "reduce", "dump")
+
+DTYPES = {"fp32": CORR_FP32, "fp16": CORR_FP16, "fp8": CORR_FP8E4M3, "fp32_simt": CORR_FP32_SIMT}
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+
+_SIGS = {
+    "corr_create": (_int, [ctypes.POINTER(_vp), _int, _int, _int]),
+    "corr_set_stream": (_int, [_vp, _vp]),
+    "corr_set_chunk": (_int, [_vp, _i64]),
+    "corr_set_corrections": (_int, [_vp, _vp, _vp]),
+    "corr_push": (_int, [_vp, _vp, _i64]),
+    "corr_dump": (_int, [_vp, _vp, ctypes.POINTER(_i64), _int]),
+    "corr_sync": (_int, [_vp]),
+    "corr_destroy": (None, [_vp]),
+    "corr_last_error": (ctypes.c_char_p, [_vp]),
+    "corr_info": (_int, [_vp] + [ctypes.POINTER(_int)] * 5),
+    "corr_profile_enable": (_int, [_vp, _int]),
+    "corr_profile_read": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double), _int]),
+    "corr_debug_spectra": (_int, [_vp, _vp, _i64, _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+class CorrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def _check(rc, h):
+    if rc != CORR_OK:
+        msg = _lib.corr_last_error(h)
+        raise CorrError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _addr(buf):
+    """Address of a tensor / ndarray / int buffer (None -> NULL)."""
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("buffer must be contiguous")
+        return buf.data_ptr()
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffer must be C-contiguous")
+        return buf.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(buf)!r}")
+
+
+# ----------------------------------------------------------------------------
+# Same-name wrappers of the C entry points
+# ----------------------------------------------------------------------------
+
+def corr_create(N, K, dtype=CORR_FP32):
+    h = _vp()
+    dtype = DTYPES.get(dtype, dtype) if isinstance(dtype, str) else dtype
+    rc = _lib.corr_create(ctypes.byref(h), int(N), int(K), int(dtype))
+    _check(rc, None)
+    return h
+
+
+def corr_set_stream(h, stream):
+    s = stream if isinstance(stream, int) or stream is None else stream.cuda_stream
+    return _check(_lib.corr_set_stream(h, s), h)
+
+
+def corr_set_chunk(h, max_spectra):
+    return _check(_lib.corr_set_chunk(h, int(max_spectra)), h)
+
+
+def corr_set_corrections(h, gains=None, delays=None):
+    """gains: complex64 [N] (tensor/ndarray) or float32 [2N]; delays: float32 [N]."""
+    return _check(_lib.corr_set_corrections(h, _addr(gains), _addr(delays)), h)
+
+
+def corr_push(h, samples, n):
+    return _check(_lib.corr_push(h, _addr(samples), int(n)), h)
+
+
+def corr_dump(h, vis, fp64=False):
+    n = _i64(0)
+    _check(_lib.corr_dump(h, _addr(vis), ctypes.byref(n), 1 if fp64 else 0), h)
+    return n.value
+
+
+def corr_sync(h):
+    return _check(_lib.corr_sync(h), h)
+
+
+def corr_destroy(h):
+    _lib.corr_destroy(h)
+
+
+def corr_last_error(h=None):
+    m = _lib.corr_last_error(h)
+    return m.decode() if m else ""
+
+
+def corr_info(h):
+    vals = [_int() for _ in range(5)]
+    _check(_lib.corr_info(h, *[ctypes.byref(v) for v in vals]), h)
+    return dict(zip(("N", "K", "C", "P", "dtype"), (v.value for v in vals)))
+
+
+def corr_profile_enable(h, on=True):
+    return _check(_lib.corr_profile_enable(h, 1 if on else 0), h)
+
+
+def corr_profile_read(h):
+    """{class: (launches, total_ms)} since the last read (clears the counters)."""
+    n = len(KERNEL_CLASSES)
+    launches = (_i64 * n)()
+    ms = (ctypes.c_double * n)()
+    _check(_lib.corr_profile_read(h, launches, ms, n), h)
+    return {c: (launches[i], ms[i]) for i, c in enumerate(KERNEL_CLASSES)}
+
+
+def corr_debug_spectra(h, samples, n, spectra):
+    return _check(_lib.corr_debug_spectra(h, _addr(samples), int(n), _addr(spectra)), h)
+
+
+# ----------------------------------------------------------------------------
+# Convenience object
+# ----------------------------------------------------------------------------
+
+class Correlator:
+    """Owning wrapper: ``with Correlator(44, 512) as c: c.push(x); V, n = c.dump()``."""
+
+    def __init__(self, N, K, dtype=CORR_FP32, chunk=None, stream=None):
+        self.h = corr_create(N, K, dtype)
+        info = corr_info(self.h)
+        self.N, self.K, self.C, self.P, self.dtype = (info[k] for k in ("N", "K", "C", "P", "dtype"))
+        if chunk is not None:
+            corr_set_chunk(self.h, chunk)
+        if stream is not None:
+            corr_set_stream(self.h, stream)
+
+    def set_corrections(self, gains=None, delays=None):
+        corr_set_corrections(self.h, gains, delays)
+
+    def push(self, samples, n=None):
+        """``samples``: uint8 buffer [n/K][N][K/2]; n defaults to its size."""
+        if n is None:
+            nbytes = samples.numel() if hasattr(samples, "numel") else np.asarray(samples).size
+            n = nbytes * 2 // self.N
+        corr_push(self.h, samples, n)
+
+    def dump(self, out=None, fp64=False):
+        """Returns (V, n_spec); V is ``out`` or a new numpy complex array [P][C]."""
+        if out is None:
+            out = np.empty((self.P, self.C), np.complex128 if fp64 else np.complex64)
+        n = corr_dump(self.h, out, fp64)
+        return out, n
+
+    def close(self):
+        if self.h is not None:
+            corr_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

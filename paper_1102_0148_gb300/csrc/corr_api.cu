@@ -1,0 +1,526 @@
+// C ABI of gbcorr (declared in include/corr.h): handle lifecycle, workspace
+// plan, the push loop that drives F-engine -> X-engine -> FP64 reduction per
+// workspace pass, and the dump.
+#include "corr_internal.h"
+#include "xengine_tc.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace gbcorr;
+
+namespace {
+
+constexpr int64_t kDefaultChunk = 2048;
+constexpr int64_t kSimtSplit = 256;   // frames per SIMT X-engine split
+
+thread_local std::string g_create_error = "no error";
+
+}  // namespace
+
+struct corr_s {
+    int N = 0, K = 0, C = 0, P = 0, dtype = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t copy_stream = nullptr;
+    int64_t cap = 0;             // frames per workspace pass (multiple of kSpecPad)
+    int spec_type = SPEC_F32;
+    bool use_tc = false;
+    void* spec = nullptr;
+    float2* twiddle = nullptr;   // W_K^m, m in [0, K)
+    float2* corr_tab = nullptr;  // [N][C]
+    bool corr_on = false;
+    float2* gains_dev = nullptr;
+    float* delays_dev = nullptr;
+    float* scale = nullptr;      // [N][C] pre-cast scales (FP16 / FP8)
+    double2* acc = nullptr;      // [C][P]
+    float2* partial = nullptr;   // [max_split][C][P]
+    int max_split = 0;
+    int* status = nullptr;       // device-side error word
+    uint8_t* stage[2] = {nullptr, nullptr};
+    cudaEvent_t stage_free[2] = {nullptr, nullptr};
+    cudaEvent_t stage_full[2] = {nullptr, nullptr};
+    int stage_next = 0;
+    void* vis_dev = nullptr;
+    int64_t n_spec = 0;
+    TcPlan* tc = nullptr;
+    // instrumentation: CUDA event pairs per kernel class
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[CORR_KERNEL_COUNT];
+    int64_t prof_launches[CORR_KERNEL_COUNT] = {0, 0, 0, 0};
+    double prof_ms[CORR_KERNEL_COUNT] = {0, 0, 0, 0};
+    cudaEvent_t ev_open = nullptr;
+    std::string err = "no error";
+};
+
+namespace {
+
+int set_err(corr_t h, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h)
+        h->err = buf;
+    else
+        g_create_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(h, call)                                                                 \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return set_err((h), e_ == cudaErrorMemoryAllocation ? CORR_ENOMEM : CORR_ECUDA, \
+                           "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,      \
+                           __LINE__);                                                     \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int spec_type_for(int dtype) {
+    if (dtype == CORR_FP16) return SPEC_F16;
+    if (dtype == CORR_FP8E4M3) return SPEC_F8;
+    return SPEC_F32;
+}
+
+void free_workspace(corr_t h) {
+    cudaFree(h->spec);
+    h->spec = nullptr;
+    cudaFree(h->partial);
+    h->partial = nullptr;
+}
+
+int alloc_workspace(corr_t h, int64_t cap) {
+    cap = (cap + kSpecPad - 1) / kSpecPad * kSpecPad;
+    const size_t eb = (size_t)spec_elem_bytes(h->spec_type);
+    const size_t spec_bytes = (size_t)h->C * 2 * h->N * cap * eb;
+    const int max_split = (int)((cap + kSimtSplit - 1) / kSimtSplit);
+    void* spec = nullptr;
+    float2* part = nullptr;
+    cudaError_t e = cudaMalloc(&spec, spec_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&part, (size_t)max_split * h->C * h->P * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemsetAsync(spec, 0, spec_bytes, h->stream);
+    if (e != cudaSuccess) {
+        cudaFree(spec);
+        cudaFree(part);
+        return set_err(h, CORR_ENOMEM, "workspace allocation of %zu bytes failed: %s", spec_bytes,
+                       cudaGetErrorString(e));
+    }
+    free_workspace(h);
+    h->spec = spec;
+    h->partial = part;
+    h->cap = cap;
+    h->max_split = max_split;
+    if (h->use_tc) {
+        int rc = tc_plan_update(h->tc, h->spec, h->cap, h->N, h->C, h->spec_type, h->err);
+        if (rc != CORR_OK) return rc;
+    }
+    return CORR_OK;
+}
+
+int check_status(corr_t h) {
+    int st = 0;
+    CUDA_TRY(h, cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        CUDA_TRY(h, cudaMemset(h->status, 0, sizeof(int)));
+        return set_err(h, CORR_ETIMEOUT, "a bounded device-side wait gave up (code %d)", st);
+    }
+    return CORR_OK;
+}
+
+cudaEvent_t prof_event(corr_t h) {
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Bracket one kernel launch with events on the handle's stream (when enabled).
+void prof_begin(corr_t h) {
+    if (!h->prof_on) return;
+    h->ev_open = prof_event(h);
+    if (h->ev_open) cudaEventRecord(h->ev_open, h->stream);
+}
+
+void prof_end(corr_t h, int cls) {
+    if (!h->prof_on || !h->ev_open) return;
+    cudaEvent_t e = prof_event(h);
+    if (!e) return;
+    cudaEventRecord(e, h->stream);
+    h->ev_pending[cls].emplace_back(h->ev_open, e);
+    h->ev_open = nullptr;
+    h->prof_launches[cls] += 1;
+}
+
+// One workspace pass: S frames at `din` (device) -> accumulators.
+int run_pass(corr_t h, const uint8_t* din, int64_t S) {
+    const int64_t S_pad = (S + kSpecPad - 1) / kSpecPad * kSpecPad;
+    FengineArgs fa{};
+    fa.in = din;
+    fa.N = h->N;
+    fa.K = h->K;
+    fa.S = S;
+    fa.S_pad = S_pad;
+    fa.twiddle = h->twiddle;
+    fa.corr = h->corr_on ? h->corr_tab : nullptr;
+    fa.spec = h->spec;
+    fa.ld = h->cap;
+    fa.spec_type = h->spec_type;
+    fa.scale = (h->spec_type != SPEC_F32) ? h->scale : nullptr;
+    fa.debug_out = nullptr;
+    prof_begin(h);
+    CUDA_TRY(h, launch_fengine(fa, h->stream));
+    prof_end(h, CORR_KERNEL_FENGINE);
+
+    if (h->use_tc) {
+        prof_begin(h);
+        int rc = tc_run(h->tc, S_pad, h->partial, h->scale, h->status, h->stream, h->err);
+        if (rc != CORR_OK) return rc;
+        prof_end(h, CORR_KERNEL_XENGINE);
+        prof_begin(h);
+        CUDA_TRY(h, launch_reduce_partials(h->partial, tc_num_partials(h->tc, S_pad),
+                                           (int64_t)h->C * h->P, h->acc, h->stream));
+        prof_end(h, CORR_KERNEL_REDUCE);
+    } else {
+        XengineArgs xa{};
+        xa.spec = h->spec;
+        xa.ld = h->cap;
+        xa.N = h->N;
+        xa.C = h->C;
+        xa.S_pad = S_pad;
+        xa.spec_type = h->spec_type;
+        xa.s_per_split = kSimtSplit;
+        xa.n_split = (int)((S_pad + kSimtSplit - 1) / kSimtSplit);
+        xa.partial = h->partial;
+        xa.scale = nullptr;
+        xa.status = h->status;
+        prof_begin(h);
+        CUDA_TRY(h, launch_xengine_simt(xa, h->stream));
+        prof_end(h, CORR_KERNEL_XENGINE);
+        prof_begin(h);
+        CUDA_TRY(h, launch_reduce_partials(h->partial, xa.n_split, (int64_t)h->C * h->P, h->acc,
+                                           h->stream));
+        prof_end(h, CORR_KERNEL_REDUCE);
+    }
+    return CORR_OK;
+}
+
+void destroy_impl(corr_t h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+    free_workspace(h);
+    cudaFree(h->twiddle);
+    cudaFree(h->corr_tab);
+    cudaFree(h->gains_dev);
+    cudaFree(h->delays_dev);
+    cudaFree(h->scale);
+    cudaFree(h->acc);
+    cudaFree(h->status);
+    cudaFree(h->vis_dev);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(h->stage[b]);
+        if (h->stage_free[b]) cudaEventDestroy(h->stage_free[b]);
+        if (h->stage_full[b]) cudaEventDestroy(h->stage_full[b]);
+    }
+    if (h->tc) tc_plan_destroy(h->tc);
+    for (auto& v : h->ev_pending)
+        for (auto& pr : v) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int corr_create(corr_t* out, int N, int K, int dtype) {
+    if (!out) return set_err(nullptr, CORR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (N < 1 || N > CORR_MAX_N)
+        return set_err(nullptr, CORR_EINVAL, "N=%d outside [1, %d]", N, CORR_MAX_N);
+    if (K < 16 || K > 4096 || (K & (K - 1)))
+        return set_err(nullptr, CORR_EINVAL, "K=%d is not a power of two in [16, 4096]", K);
+    if (dtype < CORR_FP32 || dtype > CORR_FP32_SIMT)
+        return set_err(nullptr, CORR_EINVAL, "unknown dtype %d", dtype);
+
+    corr_t h = new (std::nothrow) corr_s();
+    if (!h) return set_err(nullptr, CORR_ENOMEM, "host allocation failed");
+    h->N = N;
+    h->K = K;
+    h->C = K / 2;
+    h->P = N * (N + 1) / 2;
+    h->dtype = dtype;
+    h->spec_type = spec_type_for(dtype);
+    h->use_tc = dtype != CORR_FP32_SIMT;
+
+    auto bail = [&](int rc) {
+        g_create_error = h->err;
+        destroy_impl(h);
+        return rc;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return set_err(nullptr, CORR_ECUDA, "no CUDA device available");
+    }
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(set_err(h, CORR_ECUDA, "stream creation failed"));
+    h->own_stream = true;
+    if (cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(set_err(h, CORR_ECUDA, "stream creation failed"));
+
+    if (h->use_tc) {
+        int rc = tc_plan_create(&h->tc, N, h->C, h->spec_type, h->err);
+        if (rc != CORR_OK) return bail(rc);
+    }
+
+    // Twiddles W_K^m = exp(-2 pi i m / K), from an exact integer angle in FP64.
+    std::vector<float2> tw(K);
+    for (int m = 0; m < K; ++m) {
+        const double th = 2.0 * M_PI * (double)m / (double)K;
+        tw[m] = make_float2((float)std::cos(th), (float)-std::sin(th));
+    }
+    const size_t acc_bytes = (size_t)h->C * h->P * sizeof(double2);
+    if (cudaMalloc((void**)&h->twiddle, K * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc((void**)&h->acc, acc_bytes) != cudaSuccess ||
+        cudaMalloc((void**)&h->status, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&h->corr_tab, (size_t)N * h->C * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc((void**)&h->gains_dev, (size_t)N * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc((void**)&h->delays_dev, (size_t)N * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(set_err(h, CORR_ENOMEM, "device allocation failed"));
+    }
+    if (h->spec_type != SPEC_F32) {
+        if (cudaMalloc((void**)&h->scale, (size_t)N * h->C * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(set_err(h, CORR_ENOMEM, "device allocation failed"));
+        }
+    }
+    if (cudaMemcpy(h->twiddle, tw.data(), K * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemsetAsync(h->acc, 0, acc_bytes, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess)
+        return bail(set_err(h, CORR_ECUDA, "initialisation copy failed"));
+    if (h->scale) {
+        std::vector<float> ones((size_t)N * h->C, 1.0f);
+        if (cudaMemcpy(h->scale, ones.data(), ones.size() * sizeof(float), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return bail(set_err(h, CORR_ECUDA, "initialisation copy failed"));
+    }
+    int rc = alloc_workspace(h, kDefaultChunk);
+    if (rc != CORR_OK) return bail(rc);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return bail(set_err(h, CORR_ECUDA, "initialisation failed"));
+    *out = h;
+    return CORR_OK;
+}
+
+int corr_set_stream(corr_t h, void* stream) {
+    if (!h) return CORR_EINVAL;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (h->own_stream) {
+        cudaStreamDestroy(h->stream);
+        h->own_stream = false;
+    }
+    h->stream = static_cast<cudaStream_t>(stream);
+    return CORR_OK;
+}
+
+int corr_set_chunk(corr_t h, int64_t max_spectra) {
+    if (!h) return CORR_EINVAL;
+    if (max_spectra < 1 || max_spectra > (int64_t)1 << 24)
+        return set_err(h, CORR_EINVAL, "chunk of %lld spectra outside [1, 2^24]",
+                       (long long)max_spectra);
+    if (h->n_spec != 0)
+        return set_err(h, CORR_ESTATE, "chunk size can only change between integrations");
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return alloc_workspace(h, max_spectra);
+}
+
+int corr_set_corrections(corr_t h, const float* gains, const float* delays) {
+    if (!h) return CORR_EINVAL;
+    if (!gains && !delays) {
+        h->corr_on = false;
+        return CORR_OK;
+    }
+    if (gains)
+        CUDA_TRY(h, cudaMemcpyAsync(h->gains_dev, gains, (size_t)h->N * sizeof(float2),
+                                    cudaMemcpyDefault, h->stream));
+    if (delays)
+        CUDA_TRY(h, cudaMemcpyAsync(h->delays_dev, delays, (size_t)h->N * sizeof(float),
+                                    cudaMemcpyDefault, h->stream));
+    CUDA_TRY(h, launch_correction_table(gains ? h->gains_dev : nullptr,
+                                        delays ? h->delays_dev : nullptr, h->N, h->K, h->corr_tab,
+                                        h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->corr_on = true;
+    return CORR_OK;
+}
+
+int corr_push(corr_t h, const uint8_t* samples, int64_t n) {
+    if (!h) return CORR_EINVAL;
+    if (n < 0 || n % h->K)
+        return set_err(h, CORR_EINVAL, "n=%lld is not a non-negative multiple of K=%d",
+                       (long long)n, h->K);
+    if (n == 0) return CORR_OK;
+    if (!samples) return set_err(h, CORR_EINVAL, "samples is NULL");
+    const int64_t frames = n / h->K;
+    const int64_t rec = (int64_t)h->N * (h->K / 2);
+    const bool host = !is_device_ptr(samples);
+    if (host && !h->stage[0]) {
+        for (int b = 0; b < 2; ++b) {
+            CUDA_TRY(h, cudaMalloc((void**)&h->stage[b], (size_t)(h->cap * rec)));
+            CUDA_TRY(h, cudaEventCreateWithFlags(&h->stage_free[b], cudaEventDisableTiming));
+            CUDA_TRY(h, cudaEventCreateWithFlags(&h->stage_full[b], cudaEventDisableTiming));
+        }
+    }
+    for (int64_t f0 = 0; f0 < frames; f0 += h->cap) {
+        const int64_t S = frames - f0 < h->cap ? frames - f0 : h->cap;
+        const uint8_t* din = samples + f0 * rec;
+        int b = 0;
+        if (host) {
+            b = h->stage_next;
+            h->stage_next ^= 1;
+            CUDA_TRY(h, cudaStreamWaitEvent(h->copy_stream, h->stage_free[b], 0));
+            CUDA_TRY(h, cudaMemcpyAsync(h->stage[b], din, (size_t)(S * rec), cudaMemcpyHostToDevice,
+                                        h->copy_stream));
+            CUDA_TRY(h, cudaEventRecord(h->stage_full[b], h->copy_stream));
+            CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->stage_full[b], 0));
+            din = h->stage[b];
+        }
+        int rc = run_pass(h, din, S);
+        if (rc != CORR_OK) return rc;
+        if (host) CUDA_TRY(h, cudaEventRecord(h->stage_free[b], h->stream));
+    }
+    h->n_spec += frames;
+    return CORR_OK;
+}
+
+int corr_dump(corr_t h, void* vis, int64_t* n_spec, int vis_fp64) {
+    if (!h) return CORR_EINVAL;
+    if (!vis) return set_err(h, CORR_EINVAL, "vis is NULL");
+    const size_t bytes = (size_t)h->C * h->P * (vis_fp64 ? sizeof(double2) : sizeof(float2));
+    const bool dev = is_device_ptr(vis);
+    void* out = vis;
+    if (!dev) {
+        if (!h->vis_dev) CUDA_TRY(h, cudaMalloc(&h->vis_dev, (size_t)h->C * h->P * sizeof(double2)));
+        out = h->vis_dev;
+    }
+    prof_begin(h);
+    CUDA_TRY(h, launch_dump(h->acc, h->C, h->P, out, vis_fp64, h->stream));
+    prof_end(h, CORR_KERNEL_DUMP);
+    if (!dev) CUDA_TRY(h, cudaMemcpyAsync(vis, out, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    int rc = check_status(h);
+    if (n_spec) *n_spec = h->n_spec;
+    h->n_spec = 0;
+    return rc;
+}
+
+int corr_sync(corr_t h) {
+    if (!h) return CORR_EINVAL;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return check_status(h);
+}
+
+void corr_destroy(corr_t h) { destroy_impl(h); }
+
+const char* corr_last_error(corr_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int corr_info(corr_t h, int* N, int* K, int* C, int* P, int* dtype) {
+    if (!h) return CORR_EINVAL;
+    if (N) *N = h->N;
+    if (K) *K = h->K;
+    if (C) *C = h->C;
+    if (P) *P = h->P;
+    if (dtype) *dtype = h->dtype;
+    return CORR_OK;
+}
+
+int corr_profile_enable(corr_t h, int on) {
+    if (!h) return CORR_EINVAL;
+    h->prof_on = on != 0;
+    return CORR_OK;
+}
+
+int corr_profile_read(corr_t h, int64_t* launches, double* ms, int n) {
+    if (!h) return CORR_EINVAL;
+    if (n < 0) return set_err(h, CORR_EINVAL, "n < 0");
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    for (int c = 0; c < CORR_KERNEL_COUNT; ++c) {
+        for (auto& pr : h->ev_pending[c]) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, pr.first, pr.second) == cudaSuccess) h->prof_ms[c] += t;
+            else cudaGetLastError();
+            h->ev_pool.push_back(pr.first);
+            h->ev_pool.push_back(pr.second);
+        }
+        h->ev_pending[c].clear();
+    }
+    for (int c = 0; c < n && c < CORR_KERNEL_COUNT; ++c) {
+        if (launches) launches[c] = h->prof_launches[c];
+        if (ms) ms[c] = h->prof_ms[c];
+    }
+    for (int c = 0; c < CORR_KERNEL_COUNT; ++c) {
+        h->prof_launches[c] = 0;
+        h->prof_ms[c] = 0.0;
+    }
+    return CORR_OK;
+}
+
+int corr_debug_spectra(corr_t h, const uint8_t* samples, int64_t n, float* spectra) {
+    if (!h) return CORR_EINVAL;
+    if (n < 0 || n % h->K)
+        return set_err(h, CORR_EINVAL, "n=%lld is not a non-negative multiple of K=%d",
+                       (long long)n, h->K);
+    const int64_t S = n / h->K;
+    if (S > h->cap) return set_err(h, CORR_EINVAL, "n/K=%lld exceeds the chunk size %lld",
+                                   (long long)S, (long long)h->cap);
+    if (S == 0) return CORR_OK;
+    if (!samples || !spectra) return set_err(h, CORR_EINVAL, "NULL buffer");
+    if (!is_device_ptr(samples) || !is_device_ptr(spectra))
+        return set_err(h, CORR_EINVAL, "corr_debug_spectra needs device buffers");
+    FengineArgs fa{};
+    fa.in = samples;
+    fa.N = h->N;
+    fa.K = h->K;
+    fa.S = S;
+    fa.S_pad = S;
+    fa.twiddle = h->twiddle;
+    fa.corr = h->corr_on ? h->corr_tab : nullptr;
+    fa.debug_out = reinterpret_cast<float2*>(spectra);
+    CUDA_TRY(h, launch_fengine(fa, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return CORR_OK;
+}
+
+}  // extern "C"

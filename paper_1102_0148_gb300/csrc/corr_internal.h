@@ -1,0 +1,69 @@
+// Internal declarations shared by the gbcorr translation units (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cstdint>
+#include <string>
+
+#include "corr.h"
+
+namespace gbcorr {
+
+// Element type of the corner-turned spectra workspace.
+enum SpecType { SPEC_F32 = 0, SPEC_F16 = 1, SPEC_F8 = 2 };
+
+inline int spec_elem_bytes(int t) { return t == SPEC_F32 ? 4 : (t == SPEC_F16 ? 2 : 1); }
+
+// Spectra are padded with zero frames up to a multiple of this many frames,
+// so every X-engine tile along the spectrum axis is whole.
+constexpr int kSpecPad = 128;
+
+// Arguments of one F-engine pass over S frames of one input buffer.
+struct FengineArgs {
+    const uint8_t* in;       // [S][N][K/2] packed bytes (device)
+    int N, K;
+    int64_t S;               // frames to transform
+    int64_t S_pad;           // frames written (>= S; the extra ones are zero)
+    const float2* twiddle;   // W_K^m = exp(-2 pi i m / K), m in [0, K)
+    const float2* corr;      // [N][K/2] correction a_i[k], or nullptr
+    // Corner-turned workspace: element (k, r, s) at ((k*2N + r) * ld + s),
+    // r < N real parts, r >= N imaginary parts of antenna r mod N.
+    void* spec;
+    int64_t ld;
+    int spec_type;
+    const float* scale;      // [N][K/2] pre-cast scale (FP16/FP8 only)
+    // Debug layout instead: float2 [N][S][K/2] (spec is ignored when set).
+    float2* debug_out;
+};
+
+cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st);
+
+// Correction table a[i][k] = g_i exp(-2 pi i k tau_i / K), computed in FP64.
+cudaError_t launch_correction_table(const float2* gains, const float* delays, int N, int K,
+                                    float2* table, cudaStream_t st);
+
+// SIMT X-engine over one workspace pass: partial[split][k][p] (FP32 complex).
+struct XengineArgs {
+    const void* spec;
+    int64_t ld;
+    int N, C;
+    int64_t S_pad;           // frames present (multiple of kSpecPad)
+    int spec_type;
+    int64_t s_per_split;     // frames per split (multiple of 128)
+    int n_split;
+    float2* partial;         // [n_split][C][P]
+    const float* scale;      // [N][C] pre-cast scales (FP16/FP8), else nullptr
+    int* status;             // device status word (bounded waits)
+};
+
+cudaError_t launch_xengine_simt(const XengineArgs& a, cudaStream_t st);
+
+// acc[k][p] += sum over splits of partial[split][k][p], in a fixed order (FP64).
+cudaError_t launch_reduce_partials(const float2* partial, int n_split, int64_t CP,
+                                   double2* acc, cudaStream_t st);
+
+// vis[p][k] = acc[k][p] as complex64 (fp64 == 0) or complex128; then acc = 0.
+cudaError_t launch_dump(double2* acc, int C, int P, void* vis, int fp64, cudaStream_t st);
+
+}  // namespace gbcorr

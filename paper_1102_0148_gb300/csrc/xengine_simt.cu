@@ -1,0 +1,161 @@
+// X-engine on the FP32 CUDA cores, the FP64 partial reduction and the dump.
+//
+// Paper: Sec. 1 (cross-multiply the spectra of every pair of antennas per
+// channel, accumulate to the required cadence), Sec. 4 ("complex cross
+// multiply", one complex accumulator per channel per baseline).
+//
+// V_ij[k] += Y_i conj(Y_j) = (a_i a_j + b_i b_j) + i (b_i a_j - a_i b_j) with
+// Y = a + i b.  One thread owns a 4 x 4 block of antenna pairs (block row
+// bi <= block column bj) of one channel and one range of spectra; the
+// spectra of that channel are staged in shared memory 32 frames at a time.
+#include "corr_internal.h"
+
+namespace gbcorr {
+namespace {
+
+constexpr int kTS = 32;  // frames per shared-memory tile
+
+__global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt) {
+    extern __shared__ __align__(16) float tile[];  // [kTS][2][NB4]
+    const int NB4 = nb * 4;
+    const int N = a.N;
+    const int k = blockIdx.x;
+    const int split = blockIdx.y;
+    const int t = blockIdx.z * blockDim.x + threadIdx.x;
+
+    int bi = 0, bj = 0;
+    const bool active = t < nt;
+    if (active) {
+        int rem = t;
+        while (rem >= nb - bi) {
+            rem -= nb - bi;
+            ++bi;
+        }
+        bj = bi + rem;
+    }
+    for (int e = threadIdx.x; e < kTS * 2 * NB4; e += blockDim.x) tile[e] = 0.f;
+
+    float ar[4][4], ai[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) ar[u][v] = ai[u][v] = 0.f;
+
+    const int64_t sb = (int64_t)split * a.s_per_split;
+    const int64_t se = min(a.S_pad, sb + a.s_per_split);
+    const float* base = static_cast<const float*>(a.spec) + (int64_t)k * 2 * N * a.ld;
+
+    for (int64_t s0 = sb; s0 < se; s0 += kTS) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 2 * N * kTS; e += blockDim.x) {
+            const int r = e / kTS;
+            const int c = e - r * kTS;
+            const float v = base[(int64_t)r * a.ld + s0 + c];
+            const int plane = r >= N;
+            tile[(c * 2 + plane) * NB4 + (r - plane * N)] = v;
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll 4
+            for (int c = 0; c < kTS; ++c) {
+                const float4 ri = *reinterpret_cast<const float4*>(&tile[(c * 2) * NB4 + 4 * bi]);
+                const float4 ii = *reinterpret_cast<const float4*>(&tile[(c * 2 + 1) * NB4 + 4 * bi]);
+                const float4 rj = *reinterpret_cast<const float4*>(&tile[(c * 2) * NB4 + 4 * bj]);
+                const float4 ij = *reinterpret_cast<const float4*>(&tile[(c * 2 + 1) * NB4 + 4 * bj]);
+                const float xr[4] = {ri.x, ri.y, ri.z, ri.w};
+                const float xi[4] = {ii.x, ii.y, ii.z, ii.w};
+                const float yr[4] = {rj.x, rj.y, rj.z, rj.w};
+                const float yi[4] = {ij.x, ij.y, ij.z, ij.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        ar[u][v] = fmaf(xr[u], yr[v], ar[u][v]);
+                        ar[u][v] = fmaf(xi[u], yi[v], ar[u][v]);
+                        ai[u][v] = fmaf(xi[u], yr[v], ai[u][v]);
+                        ai[u][v] = fmaf(-xr[u], yi[v], ai[u][v]);
+                    }
+            }
+        }
+    }
+    if (!active) return;
+    const int P = N * (N + 1) / 2;
+    float2* out = a.partial + ((int64_t)split * a.C + k) * P;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = 4 * bi + u;
+            const int j = 4 * bj + v;
+            if (i < N && j < N && i <= j) {
+                const int p = i * N - i * (i - 1) / 2 + (j - i);
+                out[p] = make_float2(ar[u][v], ai[u][v]);
+            }
+        }
+}
+
+__global__ void reduce_partials_kernel(const float2* part, int n_split, int64_t CP, double2* acc) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < CP;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int s = 0; s < n_split; ++s) {
+            const float2 v = part[(int64_t)s * CP + e];
+            re += (double)v.x;
+            im += (double)v.y;
+        }
+        double2 o = acc[e];
+        o.x += re;
+        o.y += im;
+        acc[e] = o;
+    }
+}
+
+__global__ void dump_kernel(double2* acc, int C, int P, void* vis, int fp64) {
+    const int64_t total = (int64_t)C * P;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int p = (int)(e / C);
+        const int k = (int)(e - (int64_t)p * C);
+        const int64_t src = (int64_t)k * P + p;
+        const double2 v = acc[src];
+        acc[src] = make_double2(0.0, 0.0);
+        if (fp64)
+            static_cast<double2*>(vis)[e] = v;
+        else
+            static_cast<float2*>(vis)[e] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+int grid_for(int64_t total) {
+    int64_t b = (total + 255) / 256;
+    return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
+
+}  // namespace
+
+cudaError_t launch_xengine_simt(const XengineArgs& a, cudaStream_t st) {
+    if (a.spec_type != SPEC_F32) return cudaErrorInvalidValue;
+    const int nb = (a.N + 3) / 4;
+    const int nt = nb * (nb + 1) / 2;
+    int threads = ((nt < 256 ? nt : 256) + 31) / 32 * 32;
+    dim3 grid((unsigned)a.C, (unsigned)a.n_split, (unsigned)((nt + threads - 1) / threads));
+    const size_t smem = (size_t)kTS * 2 * nb * 4 * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(xengine_simt_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    xengine_simt_kernel<<<grid, threads, smem, st>>>(a, nb, nt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const float2* partial, int n_split, int64_t CP, double2* acc,
+                                   cudaStream_t st) {
+    reduce_partials_kernel<<<grid_for(CP), 256, 0, st>>>(partial, n_split, CP, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dump(double2* acc, int C, int P, void* vis, int fp64, cudaStream_t st) {
+    dump_kernel<<<grid_for((int64_t)C * P), 256, 0, st>>>(acc, C, P, vis, fp64);
+    return cudaGetLastError();
+}
+
+}  // namespace gbcorr

@@ -1,0 +1,195 @@
+"""Parity of the CUDA path with the FP64 oracle, through the C ABI (GPU).
+
+Metric (the bar for the FP32 paths): for every emitted pair (i, j) and
+channel k,  e = |V_gpu - V_oracle| / sqrt(|V_ii V_jj|)  (oracle autos),
+and max e <= 1e-5.
+
+The FP32 error budget behind that bar: the F-engine's FP32 transform
+carries ~log2(K) * 2^-24 relative rounding per channel (~5e-7 at K = 512);
+the X-engine sums at most one workspace pass (<= 2048 spectra) in FP32
+before the FP64 accumulation, adding ~2^-24 sqrt(S) relative (~3e-6 at
+S = 2048) -- both well below 1e-5.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1102_0148_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+SEED = 11020148
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def vis_error(V, R, N):
+    autos = np.array([oracle.baseline_index(i, i, N) for i in range(N)])
+    A = np.abs(R[autos])
+    pairs = oracle.baseline_pairs(N)
+    ii = np.array([p[0] for p in pairs])
+    jj = np.array([p[1] for p in pairs])
+    nrm = np.sqrt(A[ii] * A[jj])
+    nrm = np.maximum(nrm, 1e-300)
+    return float(np.max(np.abs(np.asarray(V, np.complex128) - R) / nrm))
+
+
+def run_gpu(lib, torch, packed, N, K, dtype, pushes=None, chunk=None, gains=None, delays=None,
+            host=False, fp64=True):
+    c = lib.Correlator(N, K, dtype, chunk=chunk)
+    try:
+        if gains is not None or delays is not None:
+            g = None if gains is None else np.ascontiguousarray(np.asarray(gains, np.complex64))
+            d = None if delays is None else np.ascontiguousarray(np.asarray(delays, np.float32))
+            c.set_corrections(g, d)
+        buf = torch.from_numpy(np.ascontiguousarray(packed).reshape(-1))
+        if not host:
+            buf = buf.cuda()
+        rec = N * K // 2
+        F = buf.numel() // rec
+        if pushes is None:
+            pushes = [F]
+        f0 = 0
+        for nf in pushes:
+            part = buf[f0 * rec:(f0 + nf) * rec]
+            c.push(part, nf * K)
+            f0 += nf
+        assert f0 == F
+        V, n = c.dump(fp64=fp64)
+        return V, n
+    finally:
+        c.close()
+
+
+DTYPES_FP32 = ["fp32_simt"]
+
+
+@pytest.mark.parametrize("N,K,S", [(3, 16, 37), (5, 64, 130), (44, 512, 64), (7, 1024, 9),
+                                   (4, 2048, 5), (2, 4096, 3)])
+@pytest.mark.parametrize("corrected", [False, True])
+def test_fengine_spectra(lib, torch_cuda, N, K, S, corrected):
+    torch = torch_cuda
+    packed, _ = synth.make_samples(N, S * K, K, seed=SEED + K + S)
+    g, tau = synth.gains_delays(N, seed=S) if corrected else (None, None)
+    if corrected:
+        tau = tau * 7.3                      # delays beyond one sample as well
+    h = lib.corr_create(N, K, lib.CORR_FP32_SIMT)
+    try:
+        if corrected:
+            lib.corr_set_corrections(h, np.asarray(g, np.complex64), np.asarray(tau, np.float32))
+        dev = torch.from_numpy(packed.reshape(-1)).cuda()
+        out = torch.empty((N, S, K // 2), dtype=torch.complex64, device="cuda")
+        lib.corr_debug_spectra(h, dev, S * K, out)
+        Y = out.cpu().numpy()
+    finally:
+        lib.corr_destroy(h)
+    X = oracle.spectra(oracle.unpack(packed, N, K), K)
+    if corrected:
+        a = oracle.correction_factors(K, np.asarray(g, np.complex64).astype(np.complex128),
+                                      np.asarray(tau, np.float32).astype(np.float64))
+        X = X * a[:, None, :]
+    rms = np.sqrt(np.mean(np.abs(X) ** 2, axis=(1, 2)))[:, None, None]
+    err = np.max(np.abs(Y - X) / rms)
+    assert err < 5e-6, err
+
+
+@pytest.mark.parametrize("dtype", DTYPES_FP32)
+def test_cfg1_plain_fx(lib, torch_cuda, dtype):
+    """N = 44, K = 512, 2^17 samples (256 spectra), 1% correlated component."""
+    N, K, T = 44, 512, 1 << 17
+    packed, _ = synth.make_samples(N, T, K, seed=SEED + 1)
+    R, S = oracle.correlate(packed, N, K)
+    V, n = run_gpu(lib, torch_cuda, packed, N, K, dtype)
+    assert n == S == 256
+    assert V.shape == (990, 256)
+    e = vis_error(V, R, N)
+    assert e <= TOL, e
+
+
+@pytest.mark.parametrize("dtype", DTYPES_FP32)
+def test_ragged_pushes_chunks_and_corrections(lib, torch_cuda, dtype):
+    N, K = 5, 64
+    pushes = [100, 1, 200, 37]
+    S = sum(pushes)
+    packed, _ = synth.make_samples(N, S * K, K, seed=SEED + 7)
+    g, tau = synth.gains_delays(N, seed=3)
+    g32 = np.asarray(g, np.complex64)
+    t32 = np.asarray(tau, np.float32)
+    R, _ = oracle.correlate(packed, N, K, gains=g32.astype(np.complex128),
+                            delays=t32.astype(np.float64))
+    V, n = run_gpu(lib, torch_cuda, packed, N, K, dtype, pushes=pushes, chunk=128, gains=g32,
+                   delays=t32)
+    assert n == S
+    assert vis_error(V, R, N) <= TOL
+
+
+@pytest.mark.parametrize("dtype", DTYPES_FP32)
+@pytest.mark.parametrize("N,K,S", [(1, 16, 7), (2, 32, 1), (13, 128, 129), (64, 256, 200),
+                                   (65, 64, 50)])
+def test_edge_shapes(lib, torch_cuda, dtype, N, K, S):
+    packed, _ = synth.make_samples(N, S * K, K, seed=SEED + N * 1000 + K)
+    R, _ = oracle.correlate(packed, N, K)
+    V, n = run_gpu(lib, torch_cuda, packed, N, K, dtype)
+    assert n == S
+    assert vis_error(V, R, N) <= TOL
+
+
+@pytest.mark.parametrize("dtype", DTYPES_FP32)
+def test_host_and_device_inputs_agree(lib, torch_cuda, dtype):
+    N, K, S = 6, 128, 300
+    packed, _ = synth.make_samples(N, S * K, K, seed=SEED + 9)
+    Vd, _ = run_gpu(lib, torch_cuda, packed, N, K, dtype, pushes=[150, 150], chunk=128)
+    Vh, _ = run_gpu(lib, torch_cuda, packed, N, K, dtype, pushes=[150, 150], chunk=128, host=True)
+    assert np.array_equal(Vd, Vh)
+
+
+def test_dump_resets_and_errors_leave_state(lib, torch_cuda):
+    torch = torch_cuda
+    N, K, S = 4, 32, 64
+    packed, _ = synth.make_samples(N, S * K, K, seed=SEED + 11)
+    R, _ = oracle.correlate(packed, N, K)
+    c = lib.Correlator(N, K, lib.CORR_FP32_SIMT)
+    try:
+        dev = torch.from_numpy(packed.reshape(-1)).cuda()
+        c.push(dev, 0)
+        with pytest.raises(lib.CorrError) as ei:
+            c.push(dev, K + 1)
+        assert ei.value.code == lib.CORR_EINVAL
+        c.push(dev, S * K)
+        V, n = c.dump(fp64=True)
+        assert n == S and vis_error(V, R, N) <= TOL
+        V32, n2 = c.dump()
+        assert n2 == 0 and V32.dtype == np.complex64 and not np.any(V32)
+        c.push(dev, S * K)
+        out = torch.empty((c.P, c.C), dtype=torch.complex64, device="cuda")
+        n3 = lib.corr_dump(c.h, out)
+        assert n3 == S
+        np.testing.assert_allclose(out.cpu().numpy(), V.astype(np.complex64), rtol=1e-6,
+                                   atol=1e-6 * np.abs(V).max())
+    finally:
+        c.close()
+
+
+def test_profiler_counts_launches(lib, torch_cuda):
+    torch = torch_cuda
+    N, K, S = 4, 64, 300
+    packed, _ = synth.make_samples(N, S * K, K, seed=SEED + 12)
+    c = lib.Correlator(N, K, lib.CORR_FP32_SIMT, chunk=128)
+    try:
+        lib.corr_profile_enable(c.h, True)
+        c.push(torch.from_numpy(packed.reshape(-1)).cuda(), S * K)
+        c.dump()
+        prof = lib.corr_profile_read(c.h)
+        assert prof["fengine"][0] == 3 and prof["xengine"][0] == 3
+        assert prof["reduce"][0] == 3 and prof["dump"][0] == 1
+        assert all(ms >= 0 for _, ms in prof.values())
+        assert lib.corr_profile_read(c.h)["fengine"][0] == 0
+    finally:
+        c.close()

@@ -126,8 +126,9 @@ int corr_sync(corr_t h);
 /* Release everything the handle owns.  NULL is a no-op. */
 void corr_destroy(corr_t h);
 
-/* Message of the last failed call on h (or of this thread's last failed
- * corr_create when h is NULL).  Never NULL; valid until the next call. */
+/* Message of the last failed call on h (or, when h is NULL, of this thread's
+ * last failed corr_create or corr_correlate_noalloc).  Never NULL; valid
+ * until the next call. */
 const char* corr_last_error(corr_t h);
 
 /* Sizes of a handle: any pointer may be NULL. */
@@ -156,6 +157,34 @@ int corr_profile_read(corr_t h, int64_t* launches, double* ms, int n);
  * [N][n/K][C] complex64 (device memory).  Leaves the integration untouched;
  * n/K must not exceed the chunk size.  Synchronises the handle's stream. */
 int corr_debug_spectra(corr_t h, const uint8_t* samples, int64_t n, float* spectra);
+
+/* One-shot correlation that allocates no memory (the paper has no
+ * counterpart; it exists for callers that must not allocate: a real-time
+ * acquisition loop in which cudaMalloc/cudaFree could synchronise the device
+ * and stall it, or a process whose device memory is all owned by another
+ * allocator).
+ *
+ * Correlates n samples per antenna of `samples` (device memory, layout as
+ * for corr_push, n a multiple of K) and writes V, summed over all n/K
+ * spectra, to `vis` (device memory, [P][C] complex64), with the FP32
+ * CUDA-core kernels of a CORR_FP32_SIMT handle and no corrections.  Work is
+ * queued on `stream` (a cudaStream_t; NULL = legacy default stream) and the
+ * call returns without waiting for it.
+ *
+ * Scratch: every intermediate buffer lives in one 32 MiB array compiled into
+ * the library (each GPU that loads the library holds it until the process
+ * exits).  Configurations whose scratch for one 128-frame pass exceeds it --
+ * K*8 + N(N+1)/2 * K/2 * 24 + 128 * K * N * 4 bytes, each term rounded up to
+ * 256 -- are rejected with CORR_EINVAL and a message stating both sizes
+ * (N = 44, K = 512 fits).  The first call on each device looks up the
+ * array's device address with cudaGetSymbolAddress while that device is
+ * current; make that first call before any stream capture.  All calls share
+ * the one array: calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race and must be serialised by the caller.
+ * Errors: CORR_EINVAL (arguments or size), CORR_ECUDA; message from
+ * corr_last_error(NULL). */
+int corr_correlate_noalloc(const uint8_t* samples, int64_t n, int N, int K, float* vis,
+                           void* stream);
 
 #ifdef __cplusplus
 }

@@ -47,6 +47,7 @@ _SIGS = {
     "corr_profile_enable": (_int, [_vp, _int]),
     "corr_profile_read": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double), _int]),
     "corr_debug_spectra": (_int, [_vp, _vp, _i64, _vp]),
+    "corr_correlate_noalloc": (_int, [_vp, _i64, _int, _int, _vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -156,6 +157,14 @@ def corr_profile_read(h):
 
 def corr_debug_spectra(h, samples, n, spectra):
     return _check(_lib.corr_debug_spectra(h, _addr(samples), int(n), _addr(spectra)), h)
+
+
+def corr_correlate_noalloc(samples, n, N, K, vis, stream=None):
+    """Allocation-free one-shot correlation into device ``vis`` ([P][C]
+    complex64); queued on ``stream`` (torch stream, raw handle or None)."""
+    s = stream if isinstance(stream, int) or stream is None else stream.cuda_stream
+    return _check(_lib.corr_correlate_noalloc(_addr(samples), int(n), int(N), int(K), _addr(vis), s),
+                  None)
 
 
 # ----------------------------------------------------------------------------

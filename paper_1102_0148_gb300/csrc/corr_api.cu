@@ -261,6 +261,8 @@ void destroy_impl(corr_t h) {
 
 }  // namespace
 
+void gbcorr::set_global_error(const char* msg) { g_create_error = msg; }
+
 extern "C" {
 
 int corr_create(corr_t* out, int N, int K, int dtype) {

@@ -66,4 +66,7 @@ cudaError_t launch_reduce_partials(const float2* partial, int n_split, int64_t C
 // vis[p][k] = acc[k][p] as complex64 (fp64 == 0) or complex128; then acc = 0.
 cudaError_t launch_dump(double2* acc, int C, int P, void* vis, int fp64, cudaStream_t st);
 
+// Message returned by corr_last_error(NULL) on this thread.
+void set_global_error(const char* msg);
+
 }  // namespace gbcorr

@@ -97,6 +97,7 @@ bool is_device_ptr(const void* p) {
 int spec_type_for(int dtype) {
     if (dtype == CORR_FP16) return SPEC_F16;
     if (dtype == CORR_FP8E4M3) return SPEC_F8;
+    if (dtype == CORR_FP32) return SPEC_F16X2;
     return SPEC_F32;
 }
 
@@ -110,7 +111,7 @@ void free_workspace(corr_t h) {
 int alloc_workspace(corr_t h, int64_t cap) {
     cap = (cap + kSpecPad - 1) / kSpecPad * kSpecPad;
     const size_t eb = (size_t)spec_elem_bytes(h->spec_type);
-    const size_t spec_bytes = (size_t)h->C * 2 * h->N * cap * eb;
+    const size_t spec_bytes = (size_t)spec_planes(h->spec_type) * h->C * 2 * h->N * cap * eb;
     const int max_split = (int)((cap + kSimtSplit - 1) / kSimtSplit);
     void* spec = nullptr;
     float2* part = nullptr;
@@ -189,8 +190,9 @@ int run_pass(corr_t h, const uint8_t* din, int64_t S) {
     fa.corr = h->corr_on ? h->corr_tab : nullptr;
     fa.spec = h->spec;
     fa.ld = h->cap;
+    fa.plane_stride = (int64_t)h->C * 2 * h->N * h->cap;
     fa.spec_type = h->spec_type;
-    fa.scale = (h->spec_type != SPEC_F32) ? h->scale : nullptr;
+    fa.scale = (h->spec_type == SPEC_F16 || h->spec_type == SPEC_F8) ? h->scale : nullptr;
     fa.debug_out = nullptr;
     prof_begin(h);
     CUDA_TRY(h, launch_fengine(fa, h->stream));
@@ -322,7 +324,7 @@ int corr_create(corr_t* out, int N, int K, int dtype) {
         cudaGetLastError();
         return bail(set_err(h, CORR_ENOMEM, "device allocation failed"));
     }
-    if (h->spec_type != SPEC_F32) {
+    if (h->spec_type == SPEC_F16 || h->spec_type == SPEC_F8) {
         if (cudaMalloc((void**)&h->scale, (size_t)N * h->C * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             return bail(set_err(h, CORR_ENOMEM, "device allocation failed"));

@@ -11,9 +11,21 @@
 namespace gbcorr {
 
 // Element type of the corner-turned spectra workspace.
-enum SpecType { SPEC_F32 = 0, SPEC_F16 = 1, SPEC_F8 = 2 };
+//   SPEC_F32    one FP32 plane (CUDA-core X-engine)
+//   SPEC_F16    one FP16 plane of scaled values (precision form)
+//   SPEC_F8     one FP8-E4M3 plane of scaled values (precision form)
+//   SPEC_F16X2  two FP16 planes, hi = fp16(x/16) and lo = fp16(x/16 - hi):
+//               ~22 significant bits, the FP32-accurate tensor-core input
+enum SpecType { SPEC_F32 = 0, SPEC_F16 = 1, SPEC_F8 = 2, SPEC_F16X2 = 3 };
 
-inline int spec_elem_bytes(int t) { return t == SPEC_F32 ? 4 : (t == SPEC_F16 ? 2 : 1); }
+inline int spec_elem_bytes(int t) {
+    return t == SPEC_F32 ? 4 : ((t == SPEC_F16 || t == SPEC_F16X2) ? 2 : 1);
+}
+inline int spec_planes(int t) { return t == SPEC_F16X2 ? 2 : 1; }
+
+// Pre-scale of the two-plane FP16 split; keeps |x|/16 below the FP16 range
+// limit for every 4-bit input up to K = 4096 (|X| <= 8K) with |g| < 3.
+constexpr float kSplitScale = 0.0625f;
 
 // Spectra are padded with zero frames up to a multiple of this many frames,
 // so every X-engine tile along the spectrum axis is whole.
@@ -31,6 +43,7 @@ struct FengineArgs {
     // r < N real parts, r >= N imaginary parts of antenna r mod N.
     void* spec;
     int64_t ld;
+    int64_t plane_stride;    // elements from the hi plane to the lo plane (SPEC_F16X2)
     int spec_type;
     const float* scale;      // [N][K/2] pre-cast scale (FP16/FP8 only)
     // Debug layout instead: float2 [N][S][K/2] (spec is ignored when set).

@@ -26,9 +26,16 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 // 4-bit two's complement: nibble v -> v for v < 8, v - 16 otherwise.
 __device__ __forceinline__ float nib(unsigned v) { return (float)((int)((v ^ 8u) & 15u) - 8); }
 
-__device__ __forceinline__ void store_spec(void* spec, int t, int64_t off, float v) {
+__device__ __forceinline__ void store_spec(void* spec, int t, int64_t off, float v,
+                                           int64_t plane_stride) {
     if (t == SPEC_F32) {
         static_cast<float*>(spec)[off] = v;
+    } else if (t == SPEC_F16X2) {
+        const float xs = v * kSplitScale;
+        const __half hi = __float2half_rn(xs);
+        const __half lo = __float2half_rn(xs - __half2float(hi));
+        static_cast<__half*>(spec)[off] = hi;
+        static_cast<__half*>(spec)[off + plane_stride] = lo;
     } else if (t == SPEC_F16) {
         static_cast<__half*>(spec)[off] = __float2half_rn(v);
     } else {
@@ -123,7 +130,187 @@ __global__ void __launch_bounds__(kThreads) fengine_generic(FengineArgs a, int F
             const int plane = row / C;
             const int k = row - plane * C;
             const int64_t off = ((int64_t)k * 2 * a.N + plane * a.N + i) * a.ld + s0 + f;
-            store_spec(a.spec, a.spec_type, off, stg[row * FT + f]);
+            store_spec(a.spec, a.spec_type, off, stg[row * FT + f], a.plane_stride);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K = 512 F-engine: 16 lanes per spectrum, 16 complex points per lane.
+//
+// The 256-point complex transform is split as n = t + 16 j (lane t, register
+// j) and k = k1 + 16 k2:
+//   Z[k1 + 16 k2] = sum_t W16^{t k2} [ W256^{t k1} sum_j z[t + 16 j] W16^{j k1} ]
+// Stage 1 is an in-register 16-point DFT over j, then the twiddle
+// W256^{t k1}, one exchange through shared memory (lane k1 gathers the 16
+// values of its k1 from every t), and stage 2 is again an in-register
+// 16-point DFT, leaving Z[k1 + 16 k2] in lane k1, register k2.  The
+// real-to-complex split needs Z[256 - k], which lives in lane (16 - k1) mod
+// 16, register 15 - k2 (register (16 - k2) mod 16 for k1 = 0): one shuffle per
+// register.
+// ---------------------------------------------------------------------------
+
+constexpr int kF512Frames = 32;     // frames per CTA (one 128-byte run per row)
+constexpr int kF512Threads = 256;   // 16 groups of 16 lanes, 2 frames per group
+constexpr int kXStride = 17;        // exchange row stride (complex), conflict-free
+constexpr int kStgStride = 33;      // staging row stride (floats), conflict-free
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// -i * a
+__device__ __forceinline__ float2 cmi(float2 a) { return make_float2(a.y, -a.x); }
+
+// 4-point forward DFT in place: X[m] = sum_j x[j] (-i)^{jm}.
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+    const float2 t0 = cadd(x0, x2), t1 = csub(x0, x2);
+    const float2 t2 = cadd(x1, x3), t3 = cmi(csub(x1, x3));
+    x0 = cadd(t0, t2);
+    x2 = csub(t0, t2);
+    x1 = cadd(t1, t3);
+    x3 = csub(t1, t3);
+}
+
+// W16^e = exp(-2 pi i e / 16) for the products e = j2 * m1 that occur.
+__device__ __forceinline__ float2 w16mul(float2 a, int e) {
+    constexpr float c8 = 0.923879532511286756f;   // cos(pi/8)
+    constexpr float s8 = 0.382683432365089772f;   // sin(pi/8)
+    constexpr float r2 = 0.707106781186547524f;   // 1/sqrt(2)
+    switch (e) {
+        case 0: return a;
+        case 1: return cmul(a, make_float2(c8, -s8));
+        case 2: return cmul(a, make_float2(r2, -r2));
+        case 3: return cmul(a, make_float2(s8, -c8));
+        case 4: return cmi(a);
+        case 6: return cmul(a, make_float2(-r2, -r2));
+        default: return cmul(a, make_float2(-c8, s8));   // e = 9
+    }
+}
+
+// 16-point forward DFT in registers, natural order in and out (radix 4 x 4).
+__device__ __forceinline__ void dft16(float2 (&x)[16]) {
+#pragma unroll
+    for (int j2 = 0; j2 < 4; ++j2) dft4(x[j2], x[4 + j2], x[8 + j2], x[12 + j2]);
+    // x[4 m1 + j2] now holds the m1-th output of column j2; apply W16^{j2 m1}
+#pragma unroll
+    for (int j2 = 1; j2 < 4; ++j2)
+#pragma unroll
+        for (int m1 = 1; m1 < 4; ++m1) x[4 * m1 + j2] = w16mul(x[4 * m1 + j2], j2 * m1);
+#pragma unroll
+    for (int m1 = 0; m1 < 4; ++m1) dft4(x[4 * m1], x[4 * m1 + 1], x[4 * m1 + 2], x[4 * m1 + 3]);
+    // x[4 m1 + m2] holds X[m1 + 4 m2]: transpose the 4 x 4 index map
+    float2 y[16];
+#pragma unroll
+    for (int m1 = 0; m1 < 4; ++m1)
+#pragma unroll
+        for (int m2 = 0; m2 < 4; ++m2) y[m1 + 4 * m2] = x[4 * m1 + m2];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) x[q] = y[q];
+}
+
+template <bool DEBUG>
+__global__ void __launch_bounds__(kF512Threads, 2) fengine_k512(FengineArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* stg = reinterpret_cast<float*>(smem_raw);                        // [512][33]
+    float2* xch = reinterpret_cast<float2*>(stg + (DEBUG ? 0 : 512 * kStgStride));  // [16][16*17]
+    float2* tw_stage = xch + 16 * 16 * kXStride;                            // [16 k1][16 t]
+    float2* tw_post = tw_stage + 256;                                       // [256]
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 15;
+    const int grp = tid >> 4;
+    const int warp = tid >> 5;
+    const int half = grp & 1;
+    const int i = blockIdx.y;
+    const int64_t s0 = (int64_t)blockIdx.x * kF512Frames;
+    const int64_t s_end = DEBUG ? a.S : a.S_pad;
+
+    // twiddle tables: W256^{t k1} = W512^{2 t k1} and W512^k
+    {
+        const int k1 = tid >> 4, t = tid & 15;
+        tw_stage[tid] = a.twiddle[2 * t * k1];
+        tw_post[tid] = a.twiddle[tid];
+    }
+
+    // prefetch both rounds' 16 bytes per lane
+    uint4 raw0 = make_uint4(0u, 0u, 0u, 0u), raw1 = raw0;
+    {
+        const int64_t sa = s0 + warp + 16 * half, sb = sa + 8;
+        if (sa < a.S) raw0 = __ldg(reinterpret_cast<const uint4*>(a.in + (sa * a.N + i) * 256) + lane);
+        if (sb < a.S) raw1 = __ldg(reinterpret_cast<const uint4*>(a.in + (sb * a.N + i) * 256) + lane);
+    }
+    __syncthreads();
+
+    float2* gx = xch + grp * 16 * kXStride;
+    unsigned char* gbytes = reinterpret_cast<unsigned char*>(gx);
+
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {
+        const int f = warp + 8 * r + 16 * half;
+        const int64_t s = s0 + f;
+        // byte transpose: lane t needs bytes t + 16 j
+        *reinterpret_cast<uint4*>(gbytes + 16 * lane) = r == 0 ? raw0 : raw1;
+        __syncwarp();
+        float2 x[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const unsigned b = gbytes[lane + 16 * j];
+            x[j] = make_float2(nib(b & 15u), nib(b >> 4));
+        }
+        __syncwarp();
+        dft16(x);
+        // twiddle W256^{t k1}, then exchange: lane k1 collects register k1 of every t
+#pragma unroll
+        for (int k1 = 1; k1 < 16; ++k1) x[k1] = cmul(x[k1], tw_stage[k1 * 16 + lane]);
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) gx[k1 * kXStride + lane] = x[k1];
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < 16; ++t) x[t] = gx[lane * kXStride + t];
+        __syncwarp();
+        dft16(x);
+        // x[q] = Z[lane + 16 q]; real-to-complex split with the partner Z[256 - k]
+        const int src = (16 - lane) & 15;
+        float2 z[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            float2 pz;
+            pz.x = __shfl_sync(0xffffffffu, x[15 - q].x, src, 16);
+            pz.y = __shfl_sync(0xffffffffu, x[15 - q].y, src, 16);
+            if (lane == 0) pz = x[(16 - q) & 15];
+            z[q] = pz;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int k = lane + 16 * q;
+            const float2 zk = x[q], zc = z[q];
+            const float2 E = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
+            const float2 O = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
+            float2 X = cadd(E, cmul(O, tw_post[k]));
+            if (a.corr) X = cmul(__ldg(a.corr + (int64_t)i * 256 + k), X);
+            if (DEBUG) {
+                if (s < a.S) a.debug_out[((int64_t)i * a.S + s) * 256 + k] = X;
+            } else {
+                if (a.scale) {
+                    const float sc = __ldg(a.scale + (int64_t)i * 256 + k);
+                    X.x *= sc;
+                    X.y *= sc;
+                }
+                stg[k * kStgStride + f] = X.x;
+                stg[(256 + k) * kStgStride + f] = X.y;
+            }
+        }
+    }
+    if (DEBUG) return;
+    __syncthreads();
+    // rows (plane, k): 32 consecutive frames each, one warp per row
+    const int nfr = (int)min((int64_t)kF512Frames, s_end - s0);
+    const int l32 = tid & 31;
+    for (int row = warp; row < 512; row += kF512Threads / 32) {
+        const int plane = row >> 8;
+        const int k = row & 255;
+        if (l32 < nfr) {
+            const int64_t off = ((int64_t)k * 2 * a.N + plane * a.N + i) * a.ld + s0 + l32;
+            store_spec(a.spec, a.spec_type, off, stg[row * kStgStride + l32], a.plane_stride);
         }
     }
 }
@@ -151,6 +338,27 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
     const int L = a.K / 2;
     const int C = L;
     const bool dbg = a.debug_out != nullptr;
+    // K = 512 with 16-byte aligned input (the fast kernel reads 16 B per lane).
+    if (a.K == 512 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0) {
+        const int64_t fr = dbg ? a.S : a.S_pad;
+        if (fr <= 0) return cudaSuccess;
+        dim3 grid((unsigned)((fr + kF512Frames - 1) / kF512Frames), (unsigned)a.N);
+        const size_t tables = (size_t)16 * 16 * kXStride * sizeof(float2) + 512 * sizeof(float2);
+        cudaError_t e;
+        if (dbg) {
+            e = cudaFuncSetAttribute(fengine_k512<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tables);
+            if (e != cudaSuccess) return e;
+            fengine_k512<true><<<grid, kF512Threads, tables, st>>>(a);
+        } else {
+            const size_t smem = tables + (size_t)512 * kStgStride * sizeof(float);
+            e = cudaFuncSetAttribute(fengine_k512<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            fengine_k512<false><<<grid, kF512Threads, smem, st>>>(a);
+        }
+        return cudaGetLastError();
+    }
     int FT = 8192 / C;
     FT = FT < 1 ? 1 : (FT > 32 ? 32 : FT);
     const int64_t frames = dbg ? a.S : a.S_pad;

@@ -68,7 +68,7 @@ def run_gpu(lib, torch, packed, N, K, dtype, pushes=None, chunk=None, gains=None
         c.close()
 
 
-DTYPES_FP32 = ["fp32_simt"]
+DTYPES_FP32 = ["fp32_simt", "fp32"]
 
 
 @pytest.mark.parametrize("N,K,S", [(3, 16, 37), (5, 64, 130), (44, 512, 64), (7, 1024, 9),
@@ -134,6 +134,8 @@ def test_ragged_pushes_chunks_and_corrections(lib, torch_cuda, dtype):
 @pytest.mark.parametrize("N,K,S", [(1, 16, 7), (2, 32, 1), (13, 128, 129), (64, 256, 200),
                                    (65, 64, 50)])
 def test_edge_shapes(lib, torch_cuda, dtype, N, K, S):
+    if dtype != "fp32_simt" and 2 * N > 128:
+        pytest.skip("the tensor-core X-engine tiles one 128-row block (N <= 64)")
     packed, _ = synth.make_samples(N, S * K, K, seed=SEED + N * 1000 + K)
     R, _ = oracle.correlate(packed, N, K)
     V, n = run_gpu(lib, torch_cuda, packed, N, K, dtype)
@@ -148,6 +150,24 @@ def test_host_and_device_inputs_agree(lib, torch_cuda, dtype):
     Vd, _ = run_gpu(lib, torch_cuda, packed, N, K, dtype, pushes=[150, 150], chunk=128)
     Vh, _ = run_gpu(lib, torch_cuda, packed, N, K, dtype, pushes=[150, 150], chunk=128, host=True)
     assert np.array_equal(Vd, Vh)
+
+
+@pytest.mark.parametrize("dtype", DTYPES_FP32)
+def test_unaligned_input_pointer(lib, torch_cuda, dtype):
+    """An input that does not start on a 16-byte boundary takes the byte-wise
+    F-engine and gives the same visibilities."""
+    torch = torch_cuda
+    N, K, S = 44, 512, 40
+    packed, _ = synth.make_samples(N, S * K, K, seed=SEED + 13)
+    R, _ = oracle.correlate(packed, N, K)
+    raw = torch.zeros(packed.size + 16, dtype=torch.uint8, device="cuda")
+    raw[3:3 + packed.size] = torch.from_numpy(packed.reshape(-1)).cuda()
+    view = raw[3:3 + packed.size]
+    assert view.data_ptr() % 16 == 3
+    with lib.Correlator(N, K, dtype) as c:
+        c.push(view, S * K)
+        V, n = c.dump(fp64=True)
+    assert n == S and vis_error(V, R, N) <= TOL
 
 
 def test_dump_resets_and_errors_leave_state(lib, torch_cuda):
@@ -193,3 +213,22 @@ def test_profiler_counts_launches(lib, torch_cuda):
         assert lib.corr_profile_read(c.h)["fengine"][0] == 0
     finally:
         c.close()
+
+
+# Precision forms: single-plane FP16 / FP8-E4M3 tensor-core inputs.  Stated
+# bounds on the normalised error against the FP64 oracle (cfg1 input):
+# FP16 carries 2^-11 relative rounding per element, ~1e-4 after 256
+# spectra; FP8-E4M3 carries 2^-4, ~1e-2.
+PRECISION_BOUND = {"fp16": 1e-3, "fp8": 5e-2}
+
+
+@pytest.mark.parametrize("dtype", ["fp16", "fp8"])
+def test_precision_forms_cfg1(lib, torch_cuda, dtype):
+    N, K, T = 44, 512, 1 << 17
+    packed, _ = synth.make_samples(N, T, K, seed=SEED + 1)
+    R, S = oracle.correlate(packed, N, K)
+    V, n = run_gpu(lib, torch_cuda, packed, N, K, dtype)
+    assert n == S
+    e = vis_error(V, R, N)
+    print(f"{dtype}: normalised error vs FP64 oracle {e:.3g}")
+    assert e <= PRECISION_BOUND[dtype], e

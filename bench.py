@@ -44,6 +44,14 @@ SEED = 11020148 + 2
 # 770e6 B/s of 4-bit samples = 1.54e9 antenna-samples/s (Sec. 1, abstract).
 PAPER_RATE = N_ANT * RATE
 
+# DRAM bytes (read + write) of one full 2048-frame launch of the dominant
+# kernel, from one ncu capture of the current kernels (summaries under
+# profiles/); scaled to the average launch below.  Remove an entry when its
+# kernel changes.
+NCU_TRAFFIC_2048 = {
+    ("fengine", "fp32"): (23.104512e6 + 129.517568e6, "profiles/fx_n44_k512_35msps_fp32.md"),
+}
+
 WORKLOAD = ("N=44 antennas, K=512-point real FFT -> 256 channels, 990 outputs/channel, "
             "35 MS/s, 1 s integration = 68359 spectra per step in 2^20-sample pushes")
 
@@ -59,6 +67,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="spectra per internal pass (corr_set_chunk); 0 = library default")
     return ap.parse_args()
 
 
@@ -252,6 +262,8 @@ def main():
     dev_in = dev_in.reshape(-1)
     stream = torch.cuda.current_stream()
     h = corr.corr_create(N_ANT, K_FFT, dtype)
+    if args.chunk:
+        corr.corr_set_chunk(h, args.chunk)
     corr.corr_set_stream(h, stream.cuda_stream)
     info_h = corr.corr_info(h)
     P, C = info_h["P"], info_h["C"]
@@ -323,8 +335,13 @@ def main():
         peak = hbm_peak
         psrc = f"{peak_src} hbm_gbs"
         achieved = work / (ms / n_launch / 1e3) / 1e9
+    traffic = None
+    tr = NCU_TRAFFIC_2048.get((dom, args.dtype))
+    if tr and not args.chunk:
+        traffic = tr[0] * (spec_total / n_launch) / CHUNK_FRAMES
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "peak_source": psrc,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": tr[1] if traffic else None, "peak_source": psrc,
                 "work_per_launch": work,
                 "kernel_ms": {c: prof[c][1] for c in prof},
                 "kernel_launches": {c: prof[c][0] for c in prof}}
@@ -362,7 +379,7 @@ def main():
     # TC vs FP32: the other X-engine precisions on the same integration
     variants = None
     if not args.no_variants and rank == 0:
-        variants = measure_variants(corr, torch, np, dev_in, pushes, rec, args.dtype)
+        variants = measure_variants(corr, torch, np, dev_in, pushes, rec, args.dtype, args.chunk)
 
     corr.corr_destroy(h)
 
@@ -380,6 +397,7 @@ def main():
             "rtf": value / (world * N_ANT * RATE),
             "config": {"workload": WORKLOAD, "x_engine": args.dtype,
                        "spectra_per_step": frames, "chunk_samples": CHUNK_FRAMES * K_FFT,
+                       "pass_spectra": args.chunk or "default",
                        "input_bytes_per_step": frames * rec,
                        "l2": "inputs (770 MB/step) larger than L2; no flush",
                        "parallelism": f"replicas x{world}"},
@@ -392,7 +410,7 @@ def main():
     return 0
 
 
-def measure_variants(corr, torch, np, dev_in, pushes, rec, main_dtype, steps=20):
+def measure_variants(corr, torch, np, dev_in, pushes, rec, main_dtype, chunk, steps=20):
     """Throughput of each X-engine precision and its normalised visibility
     error against the FP32 tensor-core path on the same 1 s integration."""
     out = {}
@@ -402,6 +420,8 @@ def measure_variants(corr, torch, np, dev_in, pushes, rec, main_dtype, steps=20)
     for name in order:
         try:
             h = corr.corr_create(N_ANT, K_FFT, corr.DTYPES[name])
+            if chunk:
+                corr.corr_set_chunk(h, chunk)
         except corr.CorrError as e:
             out[name] = {"unavailable": str(e)}
             continue

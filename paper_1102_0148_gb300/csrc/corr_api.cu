@@ -200,13 +200,17 @@ int run_pass(corr_t h, const uint8_t* din, int64_t S) {
 
     if (h->use_tc) {
         prof_begin(h);
-        int rc = tc_run(h->tc, S_pad, h->partial, h->scale, h->status, h->stream, h->err);
+        bool direct = false;
+        int rc = tc_run(h->tc, S_pad, h->partial, h->acc, h->scale, h->status, h->stream, h->err,
+                        &direct);
         if (rc != CORR_OK) return rc;
         prof_end(h, CORR_KERNEL_XENGINE);
-        prof_begin(h);
-        CUDA_TRY(h, launch_reduce_partials(h->partial, tc_num_partials(h->tc, S_pad),
-                                           (int64_t)h->C * h->P, h->acc, h->stream));
-        prof_end(h, CORR_KERNEL_REDUCE);
+        if (!direct) {
+            prof_begin(h);
+            CUDA_TRY(h, launch_reduce_partials(h->partial, tc_num_partials(h->tc, S_pad),
+                                               (int64_t)h->C * h->P, h->acc, h->stream));
+            prof_end(h, CORR_KERNEL_REDUCE);
+        }
     } else {
         XengineArgs xa{};
         xa.spec = h->spec;

@@ -207,11 +207,61 @@ __device__ __forceinline__ void dft16(float2 (&x)[16]) {
     for (int q = 0; q < 16; ++q) x[q] = y[q];
 }
 
-template <bool DEBUG>
+// Nibble v (0..15, 4-bit two's complement) to float without a conversion
+// instruction: the bit pattern 0x4B000000 | u is the float 2^23 + u.
+__device__ __forceinline__ float nib_lo(unsigned b) {
+    return __int_as_float((int)((b & 15u) ^ 0x4B000008u)) - 8388616.0f;
+}
+__device__ __forceinline__ float nib_hi(unsigned b) {
+    return __int_as_float((int)(((b >> 4) & 15u) ^ 0x4B000008u)) - 8388616.0f;
+}
+
+constexpr int kOutDebug = -1;
+constexpr int kStgRow = 513;        // staging row stride (floats): [frame][plane*256 + k]
+// staging floats, rounded up to a multiple of 4 so the exchange area after it
+// stays 16-byte aligned (its first use is a 16-byte store)
+constexpr int kStgFloats = (kF512Frames * kStgRow + 3) & ~3;
+
+// Four consecutive frames of one workspace row (channel k, row r) from the
+// staging buffer, converted and stored with one vector store per plane.
+template <int OUT>
+__device__ __forceinline__ void store4(void* spec, int64_t off, int64_t plane_stride, float v0,
+                                       float v1, float v2, float v3) {
+    if (OUT == SPEC_F32) {
+        *reinterpret_cast<float4*>(static_cast<float*>(spec) + off) = make_float4(v0, v1, v2, v3);
+    } else if (OUT == SPEC_F16) {
+        const __half2 a = __floats2half2_rn(v0, v1), b = __floats2half2_rn(v2, v3);
+        uint2 u;
+        u.x = *reinterpret_cast<const unsigned*>(&a);
+        u.y = *reinterpret_cast<const unsigned*>(&b);
+        *reinterpret_cast<uint2*>(static_cast<__half*>(spec) + off) = u;
+    } else if (OUT == SPEC_F8) {
+        const __nv_fp8x2_storage_t a = __nv_cvt_float2_to_fp8x2(make_float2(v0, v1), __NV_SATFINITE, __NV_E4M3);
+        const __nv_fp8x2_storage_t b = __nv_cvt_float2_to_fp8x2(make_float2(v2, v3), __NV_SATFINITE, __NV_E4M3);
+        *reinterpret_cast<unsigned*>(static_cast<unsigned char*>(spec) + off) =
+            (unsigned)a | ((unsigned)b << 16);
+    } else {  // SPEC_F16X2: values already carry the 1/16 pre-scale
+        const __half2 ha = __floats2half2_rn(v0, v1), hb = __floats2half2_rn(v2, v3);
+        const float2 fa = __half22float2(ha), fb = __half22float2(hb);
+        const __half2 la = __floats2half2_rn(v0 - fa.x, v1 - fa.y);
+        const __half2 lb = __floats2half2_rn(v2 - fb.x, v3 - fb.y);
+        uint2 uh, ul;
+        uh.x = *reinterpret_cast<const unsigned*>(&ha);
+        uh.y = *reinterpret_cast<const unsigned*>(&hb);
+        ul.x = *reinterpret_cast<const unsigned*>(&la);
+        ul.y = *reinterpret_cast<const unsigned*>(&lb);
+        __half* base = static_cast<__half*>(spec);
+        *reinterpret_cast<uint2*>(base + off) = uh;
+        *reinterpret_cast<uint2*>(base + off + plane_stride) = ul;
+    }
+}
+
+template <int OUT>
 __global__ void __launch_bounds__(kF512Threads, 2) fengine_k512(FengineArgs a) {
+    constexpr bool DEBUG = OUT == kOutDebug;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* stg = reinterpret_cast<float*>(smem_raw);                        // [512][33]
-    float2* xch = reinterpret_cast<float2*>(stg + (DEBUG ? 0 : 512 * kStgStride));  // [16][16*17]
+    float* stg = reinterpret_cast<float*>(smem_raw);                        // [32][513]
+    float2* xch = reinterpret_cast<float2*>(stg + (DEBUG ? 0 : kStgFloats));  // [16][16*17]
     float2* tw_stage = xch + 16 * 16 * kXStride;                            // [16 k1][16 t]
     float2* tw_post = tw_stage + 256;                                       // [256]
 
@@ -222,14 +272,19 @@ __global__ void __launch_bounds__(kF512Threads, 2) fengine_k512(FengineArgs a) {
     const int half = grp & 1;
     const int i = blockIdx.y;
     const int64_t s0 = (int64_t)blockIdx.x * kF512Frames;
-    const int64_t s_end = DEBUG ? a.S : a.S_pad;
+    // The 1/16 pre-scale of the two-plane FP16 split is folded into the
+    // real-split constants: X = c (zk + conj zc) + w'_k (zk - conj zc) with
+    // c = 1/2 and w'_k = W512^k / (2i), both times the pre-scale.
+    const float post = OUT == SPEC_F16X2 ? kSplitScale : 1.0f;
 
-    // twiddle tables: W256^{t k1} = W512^{2 t k1} and W512^k
+    // twiddle tables: W256^{t k1} = W512^{2 t k1} and w'_k
     {
         const int k1 = tid >> 4, t = tid & 15;
         tw_stage[tid] = a.twiddle[2 * t * k1];
-        tw_post[tid] = a.twiddle[tid];
+        const float2 w = a.twiddle[tid];
+        tw_post[tid] = make_float2(0.5f * post * w.y, -0.5f * post * w.x);
     }
+    const float chalf = 0.5f * post;
 
     // prefetch both rounds' 16 bytes per lane
     uint4 raw0 = make_uint4(0u, 0u, 0u, 0u), raw1 = raw0;
@@ -254,7 +309,7 @@ __global__ void __launch_bounds__(kF512Threads, 2) fengine_k512(FengineArgs a) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const unsigned b = gbytes[lane + 16 * j];
-            x[j] = make_float2(nib(b & 15u), nib(b >> 4));
+            x[j] = make_float2(nib_lo(b), nib_hi(b));
         }
         __syncwarp();
         dft16(x);
@@ -283,35 +338,37 @@ __global__ void __launch_bounds__(kF512Threads, 2) fengine_k512(FengineArgs a) {
         for (int q = 0; q < 16; ++q) {
             const int k = lane + 16 * q;
             const float2 zk = x[q], zc = z[q];
-            const float2 E = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
-            const float2 O = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
-            float2 X = cadd(E, cmul(O, tw_post[k]));
+            const float2 S = make_float2(zk.x + zc.x, zk.y - zc.y);
+            const float2 D = make_float2(zk.x - zc.x, zk.y + zc.y);
+            const float2 wd = cmul(tw_post[k], D);
+            float2 X = make_float2(fmaf(chalf, S.x, wd.x), fmaf(chalf, S.y, wd.y));
             if (a.corr) X = cmul(__ldg(a.corr + (int64_t)i * 256 + k), X);
             if (DEBUG) {
                 if (s < a.S) a.debug_out[((int64_t)i * a.S + s) * 256 + k] = X;
             } else {
-                if (a.scale) {
+                if (OUT == SPEC_F16 || OUT == SPEC_F8) {
                     const float sc = __ldg(a.scale + (int64_t)i * 256 + k);
                     X.x *= sc;
                     X.y *= sc;
                 }
-                stg[k * kStgStride + f] = X.x;
-                stg[(256 + k) * kStgStride + f] = X.y;
+                stg[f * kStgRow + k] = X.x;
+                stg[f * kStgRow + 256 + k] = X.y;
             }
         }
     }
     if (DEBUG) return;
     __syncthreads();
-    // rows (plane, k): 32 consecutive frames each, one warp per row
-    const int nfr = (int)min((int64_t)kF512Frames, s_end - s0);
+    // 512 workspace rows (plane, k) x 32 frames: a warp covers 4 rows per
+    // iteration, 8 lanes per row, 4 consecutive frames per lane.
     const int l32 = tid & 31;
-    for (int row = warp; row < 512; row += kF512Threads / 32) {
+    const int m = l32 & 7;
+    for (int row = 4 * warp + (l32 >> 3); row < 512; row += 4 * (kF512Threads / 32)) {
         const int plane = row >> 8;
         const int k = row & 255;
-        if (l32 < nfr) {
-            const int64_t off = ((int64_t)k * 2 * a.N + plane * a.N + i) * a.ld + s0 + l32;
-            store_spec(a.spec, a.spec_type, off, stg[row * kStgStride + l32], a.plane_stride);
-        }
+        const float* src = stg + 4 * m * kStgRow + row;
+        const int64_t off = ((int64_t)k * 2 * a.N + plane * a.N + i) * a.ld + s0 + 4 * m;
+        store4<OUT>(a.spec, off, a.plane_stride, src[0], src[kStgRow], src[2 * kStgRow],
+                    src[3 * kStgRow]);
     }
 }
 
@@ -344,20 +401,21 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
         if (fr <= 0) return cudaSuccess;
         dim3 grid((unsigned)((fr + kF512Frames - 1) / kF512Frames), (unsigned)a.N);
         const size_t tables = (size_t)16 * 16 * kXStride * sizeof(float2) + 512 * sizeof(float2);
-        cudaError_t e;
-        if (dbg) {
-            e = cudaFuncSetAttribute(fengine_k512<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)tables);
+        const size_t smem = dbg ? tables : tables + (size_t)kStgFloats * sizeof(float);
+        auto go = [&](auto kern) -> cudaError_t {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
             if (e != cudaSuccess) return e;
-            fengine_k512<true><<<grid, kF512Threads, tables, st>>>(a);
-        } else {
-            const size_t smem = tables + (size_t)512 * kStgStride * sizeof(float);
-            e = cudaFuncSetAttribute(fengine_k512<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            fengine_k512<false><<<grid, kF512Threads, smem, st>>>(a);
+            kern<<<grid, kF512Threads, smem, st>>>(a);
+            return cudaGetLastError();
+        };
+        if (dbg) return go(fengine_k512<kOutDebug>);
+        switch (a.spec_type) {
+            case SPEC_F32: return go(fengine_k512<SPEC_F32>);
+            case SPEC_F16: return go(fengine_k512<SPEC_F16>);
+            case SPEC_F8: return go(fengine_k512<SPEC_F8>);
+            default: return go(fengine_k512<SPEC_F16X2>);
         }
-        return cudaGetLastError();
     }
     int FT = 8192 / C;
     FT = FT < 1 ? 1 : (FT > 32 ? 32 : FT);

@@ -19,11 +19,16 @@
 //   mode 1: one FP16 plane (pre-scaled per antenna and channel).
 //   mode 2: one FP8-E4M3 plane (pre-scaled), kind::f8f6f4.
 //
-// CTA = 6 warps, persistent over work items (channel, range of spectra):
-//   warp 0   TMA producer (one lane)     -> stage ring (full/empty mbarriers)
-//   warp 1   TMEM allocator + MMA issuer (one lane) -> two TMEM accumulator sets
-//   warps 2-5 epilogue: TMEM -> registers -> G in shared memory -> V -> partials
-// The two accumulator sets let the epilogue of item n overlap the MMAs of n+1.
+// CTA = 10 warps, persistent over work items (channel, range of spectra):
+//   warp 0    TMA producer (one lane)     -> stage ring (full/empty mbarriers)
+//   warp 1    TMEM allocator + MMA issuer (one lane) -> two TMEM accumulator sets
+//   warps 2-9 epilogue: TMEM -> registers, summed over windows -> G in shared
+//             memory -> V -> partials
+// The tensor core's FP32 accumulation into TMEM is biased (it loses about one
+// unit in the last place per accumulate, always toward zero), so TMEM only
+// accumulates one window of kWindow spectra; the epilogue adds the windows
+// with round-to-nearest FP32 arithmetic.  The two accumulator sets let the
+// epilogue drain window n while the MMAs fill window n+1.
 // Every mbarrier wait is bounded by a global-timer deadline; on expiry the
 // kernel records a status code, drains its own copies and MMAs, frees TMEM
 // and returns.
@@ -38,7 +43,8 @@
 namespace gbcorr {
 namespace {
 
-constexpr int kTcThreads = 192;
+constexpr int kTcThreads = 320;   // producer, MMA, 8 epilogue warps
+constexpr int kWindow = 128;      // spectra per TMEM accumulation window
 constexpr int kRows = 128;          // MMA M = TMA box rows
 constexpr int kRowBytes = 128;      // one swizzle span per row
 constexpr int kTileBytes = kRows * kRowBytes;
@@ -51,11 +57,13 @@ struct TcArgs {
     int planes;
     int stages;
     int KT;                   // spectra per k-tile (one 128-byte row of operands)
+    int W;                    // spectra per TMEM accumulation window (multiple of KT)
     int64_t S_pad;
     int64_t S_item;           // spectra per work item (multiple of KT)
     int n_items;              // C * n_split
     uint32_t idesc;
     float2* partial;          // [n_split][C][P]
+    double2* acc;             // [C][P] FP64 accumulator, used directly when n_split == 1
     const float* scale;       // [N][C] (modes 1, 2)
     int* status;
     unsigned long long timeout_ns;
@@ -180,11 +188,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                   "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 // --------------------------------------------------------------------- kernel
 
@@ -220,7 +235,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&accf[b]), 1);
-            mbar_init(smem_u32(&acce[b]), 128);
+            mbar_init(smem_u32(&acce[b]), 256);
         }
         mbar_init(smem_u32(drain), 1);
         *abort_word = 0;
@@ -278,49 +293,54 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
     } else if (warp == 1) {
         // ------------------------------------------------------- MMA issuer
+        // One TMEM accumulation window = W spectra; windows alternate between
+        // the two accumulator sets so the epilogue drains one while the next fills.
         if (lane == 0) {
             uint32_t it = 0;
-            int li = 0;
+            int wi = 0;
             bool ok = true;
             bool issued = false;
-            for (int item = blockIdx.x; ok && item < a.n_items; item += gridDim.x, ++li) {
-                const int b = li & 1;
-                const uint32_t aph = (uint32_t)(li >> 1) & 1u;
-                if (!wait_bar(smem_u32(&acce[b]), aph ^ 1u, abort_word, a)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t d_hh = tmem + (uint32_t)b * 256u;
-                const uint32_t d_hl = d_hh + 128u;
+            for (int item = blockIdx.x; ok && item < a.n_items; item += gridDim.x) {
                 const int sp = item / a.C;
                 const int64_t s_beg = (int64_t)sp * a.S_item;
                 const int64_t s_end = min(a.S_pad, s_beg + a.S_item);
-                uint32_t acc = 0;
-                for (int64_t s = s_beg; s < s_end; s += a.KT, ++it) {
-                    const uint32_t st = it % a.stages;
-                    const uint32_t ph = (it / a.stages) & 1u;
-                    if (!wait_bar(smem_u32(&full[st]), ph, abort_word, a)) {
+                for (int64_t w0 = s_beg; ok && w0 < s_end; w0 += a.W, ++wi) {
+                    const int b = wi & 1;
+                    const uint32_t aph = (uint32_t)(wi >> 1) & 1u;
+                    if (!wait_bar(smem_u32(&acce[b]), aph ^ 1u, abort_word, a)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t base = smem_u32(stages + st * stage_bytes);
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t ad = sw128_desc(base + 32u * kk);
-                        mma<MODE>(d_hh, ad, ad, a.idesc, acc);
-                        if (planes == 2) {
-                            const uint64_t bd = sw128_desc(base + kTileBytes + 32u * kk);
-                            mma<MODE>(d_hl, ad, bd, a.idesc, acc);
+                    const uint32_t d_hh = tmem + (uint32_t)b * 256u;
+                    const uint32_t d_hl = d_hh + 128u;
+                    const int64_t w1 = min(s_end, w0 + a.W);
+                    uint32_t acc = 0;
+                    for (int64_t s = w0; s < w1; s += a.KT, ++it) {
+                        const uint32_t st = it % a.stages;
+                        const uint32_t ph = (it / a.stages) & 1u;
+                        if (!wait_bar(smem_u32(&full[st]), ph, abort_word, a)) {
+                            ok = false;
+                            break;
                         }
-                        acc = 1;
+                        tc_fence_after();
+                        const uint32_t base = smem_u32(stages + st * stage_bytes);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t ad = sw128_desc(base + 32u * kk);
+                            mma<MODE>(d_hh, ad, ad, a.idesc, acc);
+                            if (planes == 2) {
+                                const uint64_t bd = sw128_desc(base + kTileBytes + 32u * kk);
+                                mma<MODE>(d_hl, ad, bd, a.idesc, acc);
+                            }
+                            acc = 1;
+                        }
+                        issued = true;
+                        mma_commit(smem_u32(&empty[st]));
                     }
-                    issued = true;
-                    mma_commit(smem_u32(&empty[st]));
+                    if (!ok) break;
+                    mma_commit(smem_u32(&accf[b]));
                 }
-                if (!ok) break;
-                mma_commit(smem_u32(&accf[b]));
             }
             if (!ok && issued) {
                 // drain: wait for every MMA this thread issued before TMEM is freed
@@ -332,73 +352,115 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
     } else {
         // --------------------------------------------------------- epilogue
-        const int et = threadIdx.x - 64;            // 0..127
-        const int q = warp & 3;                     // TMEM lane quadrant of this warp
-        const int r = 32 * q + lane;                // accumulator row
+        // 8 warps: warp w reads TMEM lane quadrant w % 4 (rows 32q..32q+31) and
+        // one half of the Nn accumulator columns.  Windows are summed in
+        // registers with round-to-nearest FP32 adds (the tensor core's own
+        // accumulation is only trusted over one short window).
+        const int et = threadIdx.x - 64;            // 0..255
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
+        const int r = 32 * q + lane;
+        const int NH = a.Nn >> 1;                   // columns per half, multiple of 8
+        const int col0 = h * NH;
         const int N = a.N, R2 = a.R2, C = a.C, P = a.P;
-        int li = 0;
-        for (int item = blockIdx.x; item < a.n_items; item += gridDim.x, ++li) {
+        int wi = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; ok && item < a.n_items; item += gridDim.x) {
             const int k = item % C;
             const int sp = item / C;
-            const int b = li & 1;
-            const uint32_t aph = (uint32_t)(li >> 1) & 1u;
-            if (et == 0) *epi_ok = wait_bar(smem_u32(&accf[b]), aph, abort_word, a) ? 1 : 0;
-            epi_sync();
-            if (!*epi_ok) break;
-            tc_fence_after();
-            const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)b * 256u;
-            for (int c0 = 0; c0 < a.Nn; c0 += 16) {
-                uint32_t v[16];
-                tmem_ld16(trow + c0, v);
-                if (planes == 2) {
-                    uint32_t w[16];
-                    tmem_ld16(trow + 128u + c0, w);
-                    tmem_ld_wait();
+            const int64_t s_beg = (int64_t)sp * a.S_item;
+            const int64_t s_end = min(a.S_pad, s_beg + a.S_item);
+            float g[64], t[64];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(w[j]));
-                } else {
-                    tmem_ld_wait();
-                }
-                if (r < R2) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (c0 + j < R2) Gs[r * ldg + c0 + j] = __uint_as_float(v[j]);
-                }
+            for (int j = 0; j < 64; ++j) {
+                g[j] = 0.f;
+                t[j] = 0.f;
             }
-            if (planes == 2) {
-                // G[c][r] += Dhl[r][c]: element (c, r) is touched by thread r only
+            for (int64_t w0 = s_beg; w0 < s_end; w0 += a.W, ++wi) {
+                const int b = wi & 1;
+                const uint32_t aph = (uint32_t)(wi >> 1) & 1u;
+                if (et == 0) *epi_ok = wait_bar(smem_u32(&accf[b]), aph, abort_word, a) ? 1 : 0;
                 epi_sync();
-                for (int c0 = 0; c0 < a.Nn; c0 += 16) {
-                    uint32_t w[16];
-                    tmem_ld16(trow + 128u + c0, w);
-                    tmem_ld_wait();
-                    if (r < R2) {
+                if (!*epi_ok) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t trow =
+                    tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)b * 256u + (uint32_t)col0;
 #pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (c0 + j < R2) Gs[(c0 + j) * ldg + r] += __uint_as_float(w[j]);
+                for (int c = 0; c < 8; ++c) {
+                    if (8 * c < NH) {
+                        uint32_t v[8];
+                        tmem_ld8(trow + 8u * c, v);
+                        if (planes == 2) {
+                            uint32_t w[8];
+                            tmem_ld8(trow + 128u + 8u * c, w);
+                            tmem_ld_wait();
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const float wf = __uint_as_float(w[j]);
+                                g[8 * c + j] += __uint_as_float(v[j]) + wf;
+                                t[8 * c + j] += wf;
+                            }
+                        } else {
+                            tmem_ld_wait();
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) g[8 * c + j] += __uint_as_float(v[j]);
+                        }
                     }
                 }
+                tc_fence_before();
+                mbar_arrive(smem_u32(&acce[b]));   // this TMEM set may be refilled now
             }
-            tc_fence_before();
-            mbar_arrive(smem_u32(&acce[b]));       // this TMEM set may be reused now
+            if (!ok) break;
+            if (r < R2) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int col = col0 + 8 * c + j;
+                        if (8 * c < NH && col < R2) Gs[r * ldg + col] = g[8 * c + j];
+                    }
+            }
             epi_sync();
+            if (planes == 2) {
+                // G[col][r] += Dhl[r][col]: each element is touched by one thread here
+                if (r < R2) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int col = col0 + 8 * c + j;
+                            if (8 * c < NH && col < R2) Gs[col * ldg + r] += t[8 * c + j];
+                        }
+                }
+                epi_sync();
+            }
             const float gs = MODE == 0 ? 1.0f / (kSplitScale * kSplitScale) : 1.0f;
             float2* out = a.partial + ((int64_t)sp * C + k) * P;
             int i = 0;
             int row_next = N;                       // first p of row i + 1
-            for (int p = et; p < P; p += 128) {
+            for (int p = et; p < P; p += 256) {
                 while (p >= row_next) {
                     ++i;
                     row_next += N - i;
                 }
                 const int j = i + (p - (row_next - (N - i)));
-                float re = Gs[i * ldg + j] + Gs[(N + i) * ldg + N + j];
-                float im = Gs[(N + i) * ldg + j] - Gs[i * ldg + N + j];
+                const float re = Gs[i * ldg + j] + Gs[(N + i) * ldg + N + j];
+                const float im = Gs[(N + i) * ldg + j] - Gs[i * ldg + N + j];
                 float f = gs;
-                if (MODE != 0) f = 1.0f / (__ldg(a.scale + (int64_t)i * C + k) *
-                                           __ldg(a.scale + (int64_t)j * C + k));
-                out[p] = make_float2(re * f, im * f);
+                if (MODE != 0)
+                    f = 1.0f / (__ldg(a.scale + (int64_t)i * C + k) * __ldg(a.scale + (int64_t)j * C + k));
+                if (a.acc) {
+                    double2* d = a.acc + (int64_t)k * P + p;   // sole owner of (k, p) here
+                    double2 v = *d;
+                    v.x += (double)(re * f);
+                    v.y += (double)(im * f);
+                    *d = v;
+                } else {
+                    out[p] = make_float2(re * f, im * f);
+                }
             }
             epi_sync();
         }
@@ -550,8 +612,9 @@ static void choose_split(const TcPlan* p, int64_t S_pad, int& n_split, int64_t& 
         const int64_t rounds = (items + p->num_sms - 1) / p->num_sms;
         const double work = (double)rounds * (double)(per + 2);   // +2: per-item overhead
         const double eff = (double)(tiles * p->C) / ((double)p->num_sms * work);
-        if (eff > best + 1e-9) {
-            best = eff;
+        const double bonus = nn == 1 ? 1.15 : 1.0;   // n = 1 needs no reduction launch
+        if (eff * bonus > best + 1e-9) {
+            best = eff * bonus;
             n_split = nn;
             S_item = per * p->KT;
         }
@@ -565,8 +628,9 @@ int tc_num_partials(const TcPlan* p, int64_t S_pad) {
     return n;
 }
 
-int tc_run(TcPlan* p, int64_t S_pad, float2* partial, const float* scale, int* status,
-           cudaStream_t st, std::string& err) {
+int tc_run(TcPlan* p, int64_t S_pad, float2* partial, double2* acc, const float* scale,
+           int* status, cudaStream_t st, std::string& err, bool* direct) {
+    *direct = false;
     if (!p->have_map) {
         err = "tensor-core plan has no workspace";
         return CORR_ESTATE;
@@ -582,12 +646,14 @@ int tc_run(TcPlan* p, int64_t S_pad, float2* partial, const float* scale, int* s
     a.planes = p->planes;
     a.stages = p->stages;
     a.KT = p->KT;
+    a.W = kWindow;
     a.S_pad = S_pad;
     int n_split;
     choose_split(p, S_pad, n_split, a.S_item);
     a.n_items = p->C * n_split;
     a.idesc = make_idesc(kRows, p->Nn);
     a.partial = partial;
+    a.acc = (n_split == 1) ? acc : nullptr;
     a.scale = scale;
     a.status = status;
     a.timeout_ns = p->timeout_ns;
@@ -604,6 +670,7 @@ int tc_run(TcPlan* p, int64_t S_pad, float2* partial, const float* scale, int* s
         return CORR_ECUDA;
     }
     p->last_split = n_split;
+    *direct = a.acc != nullptr;
     return CORR_OK;
 }
 

@@ -1,0 +1,58 @@
+"""Full-size parity (GPU): the benchmark's workload and launch configuration.
+
+One 1 s integration of the 44-antenna, 35 MS/s, K = 512 workload (68359
+spectra, with the 0.5 LSB tone at channel 97) is pushed through the C ABI in
+2^20-sample chunks, exactly as bench.py times it.  The FP64 oracle computes
+the same bytes at a sample of channels -- DC, the tone, and three others --
+for all 990 pairs.  The FP32 paths must stay within the 1e-5 normalised
+bound at this length too: the X-engine sums at most one work item (a few
+hundred spectra) in FP32 before the FP64 accumulation, so the FP32 error
+does not grow with the integration.  The FP16 / FP8 errors are stated.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1102_0148_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+N, K, RATE = 44, 512, 35e6
+FRAMES = int(RATE // K)                   # 68359
+CHUNK = (1 << 20) // K                    # 2048 frames per push
+CHANNELS = [0, 1, 97, 170, 255]
+BOUND = {"fp32": 1e-5, "fp32_simt": 1e-5, "fp16": 1e-3, "fp8": 5e-2}
+
+
+@pytest.fixture(scope="module")
+def workload():
+    import torch
+    dev, _ = synth.make_samples_torch(N, FRAMES * K, K, seed=11020148 + 2, device="cuda",
+                                      tone_amp=0.5)
+    dev = dev.reshape(-1)
+    host = dev.cpu().numpy()
+    R, S = oracle.visibilities_channels(host, N, K, CHANNELS, frames_per_block=1024)
+    assert S == FRAMES
+    return dev, R
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "fp32_simt", "fp16", "fp8"])
+def test_one_second_integration(lib, workload, dtype):
+    dev, R = workload
+    rec = N * K // 2
+    with lib.Correlator(N, K, dtype) as c:
+        for f0 in range(0, FRAMES, CHUNK):
+            nf = min(CHUNK, FRAMES - f0)
+            lib.corr_push(c.h, dev.data_ptr() + f0 * rec, nf * K)
+        V, n = c.dump(fp64=True)
+    assert n == FRAMES
+    Vs = V[:, CHANNELS]
+    autos = np.array([oracle.baseline_index(i, i, N) for i in range(N)])
+    A = np.abs(R[autos])
+    pairs = oracle.baseline_pairs(N)
+    nrm = np.sqrt(A[[p[0] for p in pairs]] * A[[p[1] for p in pairs]])
+    e = np.abs(Vs - R) / nrm
+    per_ch = {ch: float(e[:, m].max()) for m, ch in enumerate(CHANNELS)}
+    print(f"{dtype}: max normalised error per channel {per_ch}")
+    assert max(per_ch.values()) <= BOUND[dtype], per_ch

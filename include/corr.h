@@ -108,6 +108,22 @@ int corr_set_chunk(corr_t h, int64_t max_spectra);
  * values are copied before return.  Takes effect for spectra pushed later. */
 int corr_set_corrections(corr_t h, const float* gains, const float* delays);
 
+/* Pre-cast scales of a CORR_FP16 / CORR_FP8E4M3 handle (Sec. 4: the
+ * conversion to a narrower type is preceded by prescaling).  Spectrum Y_i[k]
+ * enters the tensor cores as s_i[k] Y_i[k]; every visibility is divided by
+ * s_i[k] s_j[k] before it is accumulated, so the scales change only the
+ * rounding, never the expected value.  By default the library picks the
+ * power of two nearest (in log2) to t / sqrt(P_i[k] / 2), P = mean |Y|^2,
+ * t = 64 (FP16) or 16 (FP8):
+ * P from a 256-frame estimation pass before the first push, then from the
+ * autocorrelations V_ii[k] / n_spec of each dumped integration.
+ * corr_set_scales: `scales` = [N][C] floats (host or device) fixes the scales
+ * until corr_set_scales(h, NULL) returns to the automatic choice.
+ * corr_get_scales: copy the current scales to `scales` ([N][C] floats);
+ * CORR_ESTATE before any are known.  Both: CORR_EINVAL on other dtypes. */
+int corr_set_scales(corr_t h, const float* scales);
+int corr_get_scales(corr_t h, float* scales);
+
 /* Correlate n samples per antenna (n a multiple of K, n >= 0) and add them
  * to the running integration.  `samples` holds n/K frames in the layout
  * above (n*N/2 bytes).  Host memory is staged through the handle's pinned
@@ -133,6 +149,22 @@ const char* corr_last_error(corr_t h);
 
 /* Sizes of a handle: any pointer may be NULL. */
 int corr_info(corr_t h, int* N, int* K, int* C, int* P, int* dtype);
+
+/* Gradient of a real loss L(V) with respect to the per-antenna gains and
+ * delays applied in the F-engine (Sec. 2.1), at (gains, delays) -- N complex
+ * values as 2N floats and N floats, NULL meaning 1 and 0 -- for the
+ * visibilities of `samples` (n samples per antenna, layout as corr_push).
+ * grad_vis = dL/dRe V + i dL/dIm V, [P][C] complex64 (grad_fp64 = 0) or
+ * complex128 (PyTorch's convention for complex tensors).  Writes
+ * grad_gains = dL/dRe g + i dL/dIm g (2N floats) and grad_delays = dL/dtau
+ * (N floats).  Every buffer may be host or device memory.
+ * The uncorrected visibilities R are recomputed from the samples pass by pass
+ * (spectra are never stored) into a separate accumulator, so the running
+ * integration is untouched; then V_ij = a_i conj(a_j) R_ij gives the
+ * gradient in closed form, in FP64.  Synchronises the handle's stream. */
+int corr_grad(corr_t h, const uint8_t* samples, int64_t n, const float* gains,
+              const float* delays, const void* grad_vis, int grad_fp64, float* grad_gains,
+              float* grad_delays);
 
 /* Kernel classes reported by corr_profile_read. */
 enum corr_kernel {

@@ -48,6 +48,9 @@ _SIGS = {
     "corr_profile_read": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double), _int]),
     "corr_debug_spectra": (_int, [_vp, _vp, _i64, _vp]),
     "corr_correlate_noalloc": (_int, [_vp, _i64, _int, _int, _vp, _vp]),
+    "corr_set_scales": (_int, [_vp, _vp]),
+    "corr_grad": (_int, [_vp, _vp, _i64, _vp, _vp, _vp, _int, _vp, _vp]),
+    "corr_get_scales": (_int, [_vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -113,6 +116,20 @@ def corr_set_corrections(h, gains=None, delays=None):
     return _check(_lib.corr_set_corrections(h, _addr(gains), _addr(delays)), h)
 
 
+def corr_set_scales(h, scales=None):
+    """scales: float32 [N][C] (tensor/ndarray) or None for the automatic choice."""
+    return _check(_lib.corr_set_scales(h, _addr(scales)), h)
+
+
+def corr_get_scales(h, out=None):
+    """Current [N][C] pre-cast scales (numpy float32 unless `out` is given)."""
+    if out is None:
+        info = corr_info(h)
+        out = np.empty((info["N"], info["C"]), np.float32)
+    _check(_lib.corr_get_scales(h, _addr(out)), h)
+    return out
+
+
 def corr_push(h, samples, n):
     return _check(_lib.corr_push(h, _addr(samples), int(n)), h)
 
@@ -121,6 +138,12 @@ def corr_dump(h, vis, fp64=False):
     n = _i64(0)
     _check(_lib.corr_dump(h, _addr(vis), ctypes.byref(n), 1 if fp64 else 0), h)
     return n.value
+
+
+def corr_grad(h, samples, n, gains, delays, grad_vis, grad_fp64, grad_gains, grad_delays):
+    return _check(_lib.corr_grad(h, _addr(samples), int(n), _addr(gains), _addr(delays),
+                                 _addr(grad_vis), 1 if grad_fp64 else 0, _addr(grad_gains),
+                                 _addr(grad_delays)), h)
 
 
 def corr_sync(h):

@@ -39,7 +39,12 @@ struct corr_s {
     float2* gains_dev = nullptr;
     float* delays_dev = nullptr;
     float* scale = nullptr;      // [N][C] pre-cast scales (FP16 / FP8)
+    float scale_target = 1.0f;   // rms of each real part after scaling
+    bool scales_ready = false;   // scale[] holds valid values
+    bool scales_user = false;    // set by corr_set_scales (not updated at dumps)
     double2* acc = nullptr;      // [C][P]
+    double2* acc_raw = nullptr;  // [C][P] uncorrected visibilities for corr_grad
+    float2* grad_buf = nullptr;  // device staging for corr_grad's inputs and outputs
     float2* partial = nullptr;   // [max_split][C][P]
     int max_split = 0;
     int* status = nullptr;       // device-side error word
@@ -177,9 +182,42 @@ void prof_end(corr_t h, int cls) {
     h->prof_launches[cls] += 1;
 }
 
-// One workspace pass: S frames at `din` (device) -> accumulators.
-int run_pass(corr_t h, const uint8_t* din, int64_t S) {
+bool narrow(corr_t h) { return h->spec_type == SPEC_F16 || h->spec_type == SPEC_F8; }
+
+// First scales of a narrow-type handle: transform a short prefix of the
+// first pass (at most 256 frames, written into the still unused workspace as
+// FP32 spectra) and set s[i][k] from its mean power.
+int estimate_scales(corr_t h, const uint8_t* din, int64_t S) {
+    const size_t ws = (size_t)spec_planes(h->spec_type) * h->C * 2 * h->N * h->cap *
+                      spec_elem_bytes(h->spec_type);
+    int64_t S_est = S < 256 ? S : 256;
+    const int64_t fit = (int64_t)(ws / ((size_t)h->N * h->C * sizeof(float2)));
+    if (S_est > fit) S_est = fit;
+    if (S_est < 1) return set_err(h, CORR_EINVAL, "chunk too small to estimate scales");
+    FengineArgs fa{};
+    fa.in = din;
+    fa.N = h->N;
+    fa.K = h->K;
+    fa.S = S_est;
+    fa.S_pad = S_est;
+    fa.twiddle = h->twiddle;
+    fa.corr = h->corr_on ? h->corr_tab : nullptr;
+    fa.debug_out = static_cast<float2*>(h->spec);
+    CUDA_TRY(h, launch_fengine(fa, h->stream));
+    CUDA_TRY(h, launch_scales_from_spectra(static_cast<const float2*>(h->spec), h->N, S_est, h->C,
+                                           h->scale_target, h->scale, h->stream));
+    h->scales_ready = true;
+    return CORR_OK;
+}
+
+// One workspace pass: S frames at `din` (device) -> `acc`.  raw = true skips
+// the per-antenna corrections (the uncorrected visibilities for corr_grad).
+int run_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, double2* acc) {
     const int64_t S_pad = (S + kSpecPad - 1) / kSpecPad * kSpecPad;
+    if (narrow(h) && !h->scales_ready) {
+        int rc = estimate_scales(h, din, S);
+        if (rc != CORR_OK) return rc;
+    }
     FengineArgs fa{};
     fa.in = din;
     fa.N = h->N;
@@ -187,7 +225,7 @@ int run_pass(corr_t h, const uint8_t* din, int64_t S) {
     fa.S = S;
     fa.S_pad = S_pad;
     fa.twiddle = h->twiddle;
-    fa.corr = h->corr_on ? h->corr_tab : nullptr;
+    fa.corr = (h->corr_on && !raw) ? h->corr_tab : nullptr;
     fa.spec = h->spec;
     fa.ld = h->cap;
     fa.plane_stride = (int64_t)h->C * 2 * h->N * h->cap;
@@ -201,14 +239,14 @@ int run_pass(corr_t h, const uint8_t* din, int64_t S) {
     if (h->use_tc) {
         prof_begin(h);
         bool direct = false;
-        int rc = tc_run(h->tc, S_pad, h->partial, h->acc, h->scale, h->status, h->stream, h->err,
+        int rc = tc_run(h->tc, S_pad, h->partial, acc, h->scale, h->status, h->stream, h->err,
                         &direct);
         if (rc != CORR_OK) return rc;
         prof_end(h, CORR_KERNEL_XENGINE);
         if (!direct) {
             prof_begin(h);
             CUDA_TRY(h, launch_reduce_partials(h->partial, tc_num_partials(h->tc, S_pad),
-                                               (int64_t)h->C * h->P, h->acc, h->stream));
+                                               (int64_t)h->C * h->P, acc, h->stream));
             prof_end(h, CORR_KERNEL_REDUCE);
         }
     } else {
@@ -228,9 +266,42 @@ int run_pass(corr_t h, const uint8_t* din, int64_t S) {
         CUDA_TRY(h, launch_xengine_simt(xa, h->stream));
         prof_end(h, CORR_KERNEL_XENGINE);
         prof_begin(h);
-        CUDA_TRY(h, launch_reduce_partials(h->partial, xa.n_split, (int64_t)h->C * h->P, h->acc,
+        CUDA_TRY(h, launch_reduce_partials(h->partial, xa.n_split, (int64_t)h->C * h->P, acc,
                                            h->stream));
         prof_end(h, CORR_KERNEL_REDUCE);
+    }
+    return CORR_OK;
+}
+
+// Run every pass of n samples (host or device memory) into `acc`.
+int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, double2* acc) {
+    const int64_t frames = n / h->K;
+    const int64_t rec = (int64_t)h->N * (h->K / 2);
+    const bool host = !is_device_ptr(samples);
+    if (host && !h->stage[0]) {
+        for (int b = 0; b < 2; ++b) {
+            CUDA_TRY(h, cudaMalloc((void**)&h->stage[b], (size_t)(h->cap * rec)));
+            CUDA_TRY(h, cudaEventCreateWithFlags(&h->stage_free[b], cudaEventDisableTiming));
+            CUDA_TRY(h, cudaEventCreateWithFlags(&h->stage_full[b], cudaEventDisableTiming));
+        }
+    }
+    for (int64_t f0 = 0; f0 < frames; f0 += h->cap) {
+        const int64_t S = frames - f0 < h->cap ? frames - f0 : h->cap;
+        const uint8_t* din = samples + f0 * rec;
+        int b = 0;
+        if (host) {
+            b = h->stage_next;
+            h->stage_next ^= 1;
+            CUDA_TRY(h, cudaStreamWaitEvent(h->copy_stream, h->stage_free[b], 0));
+            CUDA_TRY(h, cudaMemcpyAsync(h->stage[b], din, (size_t)(S * rec), cudaMemcpyHostToDevice,
+                                        h->copy_stream));
+            CUDA_TRY(h, cudaEventRecord(h->stage_full[b], h->copy_stream));
+            CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->stage_full[b], 0));
+            din = h->stage[b];
+        }
+        int rc = run_pass(h, din, S, raw, acc);
+        if (rc != CORR_OK) return rc;
+        if (host) CUDA_TRY(h, cudaEventRecord(h->stage_free[b], h->stream));
     }
     return CORR_OK;
 }
@@ -246,6 +317,8 @@ void destroy_impl(corr_t h) {
     cudaFree(h->delays_dev);
     cudaFree(h->scale);
     cudaFree(h->acc);
+    cudaFree(h->acc_raw);
+    cudaFree(h->grad_buf);
     cudaFree(h->status);
     cudaFree(h->vis_dev);
     for (int b = 0; b < 2; ++b) {
@@ -290,6 +363,7 @@ int corr_create(corr_t* out, int N, int K, int dtype) {
     h->dtype = dtype;
     h->spec_type = spec_type_for(dtype);
     h->use_tc = dtype != CORR_FP32_SIMT;
+    h->scale_target = dtype == CORR_FP8E4M3 ? 16.0f : 64.0f;
 
     auto bail = [&](int rc) {
         g_create_error = h->err;
@@ -401,36 +475,56 @@ int corr_push(corr_t h, const uint8_t* samples, int64_t n) {
                        (long long)n, h->K);
     if (n == 0) return CORR_OK;
     if (!samples) return set_err(h, CORR_EINVAL, "samples is NULL");
-    const int64_t frames = n / h->K;
-    const int64_t rec = (int64_t)h->N * (h->K / 2);
-    const bool host = !is_device_ptr(samples);
-    if (host && !h->stage[0]) {
-        for (int b = 0; b < 2; ++b) {
-            CUDA_TRY(h, cudaMalloc((void**)&h->stage[b], (size_t)(h->cap * rec)));
-            CUDA_TRY(h, cudaEventCreateWithFlags(&h->stage_free[b], cudaEventDisableTiming));
-            CUDA_TRY(h, cudaEventCreateWithFlags(&h->stage_full[b], cudaEventDisableTiming));
-        }
-    }
-    for (int64_t f0 = 0; f0 < frames; f0 += h->cap) {
-        const int64_t S = frames - f0 < h->cap ? frames - f0 : h->cap;
-        const uint8_t* din = samples + f0 * rec;
-        int b = 0;
-        if (host) {
-            b = h->stage_next;
-            h->stage_next ^= 1;
-            CUDA_TRY(h, cudaStreamWaitEvent(h->copy_stream, h->stage_free[b], 0));
-            CUDA_TRY(h, cudaMemcpyAsync(h->stage[b], din, (size_t)(S * rec), cudaMemcpyHostToDevice,
-                                        h->copy_stream));
-            CUDA_TRY(h, cudaEventRecord(h->stage_full[b], h->copy_stream));
-            CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->stage_full[b], 0));
-            din = h->stage[b];
-        }
-        int rc = run_pass(h, din, S);
-        if (rc != CORR_OK) return rc;
-        if (host) CUDA_TRY(h, cudaEventRecord(h->stage_free[b], h->stream));
-    }
-    h->n_spec += frames;
+    int rc = process_samples(h, samples, n, false, h->acc);
+    if (rc != CORR_OK) return rc;
+    h->n_spec += n / h->K;
     return CORR_OK;
+}
+
+int corr_grad(corr_t h, const uint8_t* samples, int64_t n, const float* gains,
+              const float* delays, const void* grad_vis, int grad_fp64, float* grad_gains,
+              float* grad_delays) {
+    if (!h) return CORR_EINVAL;
+    if (n < 0 || n % h->K)
+        return set_err(h, CORR_EINVAL, "n=%lld is not a non-negative multiple of K=%d",
+                       (long long)n, h->K);
+    if (!samples || !grad_vis || !grad_gains || !grad_delays)
+        return set_err(h, CORR_EINVAL, "NULL buffer");
+    const size_t CPb = (size_t)h->C * h->P;
+    if (!h->acc_raw) CUDA_TRY(h, cudaMalloc((void**)&h->acc_raw, CPb * sizeof(double2)));
+    // device staging: gains (N float2), delays (N float), outputs (N float2 + N float),
+    // and the incoming gradient when it is host memory
+    const size_t gv_bytes = CPb * (grad_fp64 ? sizeof(double2) : sizeof(float2));
+    if (!h->grad_buf)
+        CUDA_TRY(h, cudaMalloc((void**)&h->grad_buf, 4 * (size_t)h->N * sizeof(float2) +
+                                                     CPb * sizeof(double2)));
+    float2* g_dev = h->grad_buf;
+    float* t_dev = reinterpret_cast<float*>(g_dev + h->N);
+    float2* gg_dev = g_dev + 2 * h->N;
+    float* gt_dev = reinterpret_cast<float*>(gg_dev + h->N);
+    void* gv_dev = g_dev + 4 * h->N;
+    if (gains)
+        CUDA_TRY(h, cudaMemcpyAsync(g_dev, gains, h->N * sizeof(float2), cudaMemcpyDefault, h->stream));
+    if (delays)
+        CUDA_TRY(h, cudaMemcpyAsync(t_dev, delays, h->N * sizeof(float), cudaMemcpyDefault, h->stream));
+    const void* gv = grad_vis;
+    if (!is_device_ptr(grad_vis)) {
+        CUDA_TRY(h, cudaMemcpyAsync(gv_dev, grad_vis, gv_bytes, cudaMemcpyHostToDevice, h->stream));
+        gv = gv_dev;
+    }
+    CUDA_TRY(h, cudaMemsetAsync(h->acc_raw, 0, CPb * sizeof(double2), h->stream));
+    if (n > 0) {
+        int rc = process_samples(h, samples, n, true, h->acc_raw);
+        if (rc != CORR_OK) return rc;
+    }
+    CUDA_TRY(h, launch_grad(h->acc_raw, gv, grad_fp64, gains ? g_dev : nullptr,
+                            delays ? t_dev : nullptr, h->N, h->K, gg_dev, gt_dev, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(grad_gains, gg_dev, h->N * sizeof(float2), cudaMemcpyDefault,
+                                h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(grad_delays, gt_dev, h->N * sizeof(float), cudaMemcpyDefault,
+                                h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return check_status(h);
 }
 
 int corr_dump(corr_t h, void* vis, int64_t* n_spec, int vis_fp64) {
@@ -442,6 +536,12 @@ int corr_dump(corr_t h, void* vis, int64_t* n_spec, int vis_fp64) {
     if (!dev) {
         if (!h->vis_dev) CUDA_TRY(h, cudaMalloc(&h->vis_dev, (size_t)h->C * h->P * sizeof(double2)));
         out = h->vis_dev;
+    }
+    if (narrow(h) && !h->scales_user && h->n_spec > 0) {
+        // the next integration is scaled from this one's autocorrelations
+        CUDA_TRY(h, launch_scales_from_autos(h->acc, h->N, h->C, h->P, h->n_spec, h->scale_target,
+                                             h->scale, h->stream));
+        h->scales_ready = true;
     }
     prof_begin(h);
     CUDA_TRY(h, launch_dump(h->acc, h->C, h->P, out, vis_fp64, h->stream));
@@ -471,6 +571,33 @@ int corr_info(corr_t h, int* N, int* K, int* C, int* P, int* dtype) {
     if (C) *C = h->C;
     if (P) *P = h->P;
     if (dtype) *dtype = h->dtype;
+    return CORR_OK;
+}
+
+int corr_set_scales(corr_t h, const float* scales) {
+    if (!h) return CORR_EINVAL;
+    if (!narrow(h)) return set_err(h, CORR_EINVAL, "scales apply to CORR_FP16 / CORR_FP8E4M3 handles");
+    if (!scales) {
+        h->scales_user = false;
+        h->scales_ready = false;
+        return CORR_OK;
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(h->scale, scales, (size_t)h->N * h->C * sizeof(float),
+                                cudaMemcpyDefault, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->scales_user = true;
+    h->scales_ready = true;
+    return CORR_OK;
+}
+
+int corr_get_scales(corr_t h, float* scales) {
+    if (!h) return CORR_EINVAL;
+    if (!narrow(h)) return set_err(h, CORR_EINVAL, "scales apply to CORR_FP16 / CORR_FP8E4M3 handles");
+    if (!scales) return set_err(h, CORR_EINVAL, "scales is NULL");
+    if (!h->scales_ready) return set_err(h, CORR_ESTATE, "no scales yet: push data or set them");
+    CUDA_TRY(h, cudaMemcpyAsync(scales, h->scale, (size_t)h->N * h->C * sizeof(float),
+                                cudaMemcpyDefault, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return CORR_OK;
 }
 

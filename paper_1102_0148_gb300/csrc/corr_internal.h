@@ -79,6 +79,20 @@ cudaError_t launch_reduce_partials(const float2* partial, int n_split, int64_t C
 // vis[p][k] = acc[k][p] as complex64 (fp64 == 0) or complex128; then acc = 0.
 cudaError_t launch_dump(double2* acc, int C, int P, void* vis, int fp64, cudaStream_t st);
 
+// Pre-cast scales s[i][k] = target / sqrt(P/2) from spectra Y[N][S][C] or from
+// the autocorrelations of the FP64 accumulator acc[C][P] over n_spec spectra.
+cudaError_t launch_scales_from_spectra(const float2* Y, int N, int64_t S, int C, float target,
+                                       float* scale, cudaStream_t st);
+cudaError_t launch_scales_from_autos(const double2* acc, int N, int C, int P, int64_t n_spec,
+                                     float target, float* scale, cudaStream_t st);
+
+// Gradient of a real loss of V with respect to the gains and delays, from the
+// uncorrected visibilities R ([C][P] FP64) and G = dL/dRe V + i dL/dIm V
+// ([P][C], complex64 or complex128).
+cudaError_t launch_grad(const double2* R, const void* G, int G_fp64, const float2* gains,
+                        const float* delays, int N, int K, float2* grad_g, float* grad_tau,
+                        cudaStream_t st);
+
 // Message returned by corr_last_error(NULL) on this thread.
 void set_global_error(const char* msg);
 

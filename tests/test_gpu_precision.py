@@ -1,0 +1,108 @@
+"""Precision form (GPU): FP16 and FP8-E4M3 tensor-core inputs with
+per-antenna, per-channel scaling from the autocorrelations, FP32
+accumulation (Sec. 4: float output converted to a narrower type with
+prescaling before the cross-multiply).
+
+Stated errors, normalised by sqrt(|V_ii V_jj|) against the FP64 oracle:
+  FP16 (11 significant bits): <= 1e-3 on a 2^20-sample prefix (2048 spectra);
+  FP8-E4M3 (4 significant bits): <= 5e-2.
+The workload is the full-band one: N = 44, 80 MS/s, K = 512, 4-bit, with the
+oracle run on the first 2^20 samples per antenna.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1102_0148_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+N, K = 44, 512
+BOUND = {"fp16": 1e-3, "fp8": 5e-2}
+
+
+def norm_err(V, R, N):
+    autos = np.array([oracle.baseline_index(i, i, N) for i in range(N)])
+    A = np.abs(R[autos])
+    pairs = oracle.baseline_pairs(N)
+    nrm = np.sqrt(A[[p[0] for p in pairs]] * A[[p[1] for p in pairs]])
+    return float(np.max(np.abs(np.asarray(V, np.complex128) - R) / np.maximum(nrm, 1e-300)))
+
+
+def correlate(lib, dev, S, dtype, scales=None):
+    with lib.Correlator(N, K, dtype) as c:
+        if scales is not None:
+            lib.corr_set_scales(c.h, scales)
+        c.push(dev, S * K)
+        V, n = c.dump(fp64=True)
+        assert n == S
+        return V
+
+
+@pytest.fixture(scope="module")
+def prefix():
+    import torch
+    S = (1 << 20) // K
+    packed, _ = synth.make_samples(N, S * K, K, seed=11020148 + 3, tone_amp=0.5)
+    R, _ = oracle.correlate(packed, N, K)
+    return torch.from_numpy(packed.reshape(-1)).cuda(), R, S
+
+
+@pytest.mark.parametrize("dtype", ["fp16", "fp8"])
+def test_full_band_prefix_error(lib, prefix, dtype):
+    dev, R, S = prefix
+    V = correlate(lib, dev, S, dtype)
+    e = norm_err(V, R, N)
+    print(f"{dtype}: normalised error vs FP64 oracle on the 2^20-sample prefix: {e:.3g}")
+    assert e <= BOUND[dtype]
+
+
+def test_scaling_prevents_fp8_saturation(lib):
+    """A 6 LSB tone puts ~1500 into channel 97, beyond FP8-E4M3's 448: with
+    unit scales the tone channel saturates, with scales from the
+    autocorrelations it does not."""
+    import torch
+    S = 256
+    packed, _ = synth.make_samples(N, S * K, K, seed=5, tone_amp=6.0)
+    R, _ = oracle.correlate(packed, N, K)
+    dev = torch.from_numpy(packed.reshape(-1)).cuda()
+    e_auto = norm_err(correlate(lib, dev, S, "fp8"), R, N)
+    ones = np.ones((N, K // 2), np.float32)
+    e_unit = norm_err(correlate(lib, dev, S, "fp8", scales=ones), R, N)
+    print(f"fp8 strong tone: auto scales {e_auto:.3g}, unit scales {e_unit:.3g}")
+    assert e_auto <= BOUND["fp8"]
+    assert e_unit > 10 * e_auto
+
+
+@pytest.mark.parametrize("dtype,target", [("fp16", 64.0), ("fp8", 16.0)])
+def test_scales_follow_autocorrelations(lib, prefix, dtype, target):
+    dev, R, S = prefix
+    with lib.Correlator(N, K, dtype) as c:
+        c.push(dev, S * K)
+        first = lib.corr_get_scales(c.h)          # from the estimation pass
+        V, n = c.dump(fp64=True)
+        after = lib.corr_get_scales(c.h)          # from this integration's autos
+    autos = np.array([oracle.baseline_index(i, i, N) for i in range(N)])
+    P = V[autos].real / n
+    want = target / np.sqrt(P / 2)
+    # powers of two, the nearest in log2 to the target scale
+    assert np.all(np.exp2(np.round(np.log2(after))) == after)
+    assert np.max(np.abs(np.log2(after / want))) <= 0.5 + 1e-9
+    # the 256-frame estimate picks the same power of two almost everywhere
+    assert np.mean(first == after) > 0.8
+
+
+def test_user_scales_do_not_bias(lib, prefix):
+    dev, R, S = prefix
+    rng = np.random.default_rng(0)
+    sc = (2.0 ** rng.integers(-3, 4, (N, K // 2))).astype(np.float32) * 16
+    V = correlate(lib, dev, S, "fp16", scales=sc)
+    assert norm_err(V, R, N) <= BOUND["fp16"]
+
+
+def test_scales_rejected_on_fp32_handles(lib):
+    with lib.Correlator(N, K, "fp32") as c:
+        with pytest.raises(lib.CorrError) as ei:
+            lib.corr_get_scales(c.h)
+        assert ei.value.code == lib.CORR_EINVAL

@@ -102,6 +102,14 @@ int corr_set_stream(corr_t h, void* stream);
  * since the last dump. */
 int corr_set_chunk(corr_t h, int64_t max_spectra);
 
+/* Tile choices of the tensor-core X-engine (no counterpart in the paper; the
+ * autotuner in paper_1102_0148_gb300/tune.py picks them): `window` = spectra
+ * accumulated in TMEM before the epilogue adds them up in FP32 (a multiple
+ * of 64, of 128 for FP8; 0 = 128), `stages` = depth of the shared-memory
+ * operand ring (2..16, clipped to what shared memory holds; 0 = automatic).
+ * CORR_EINVAL for CUDA-core handles or out-of-range values. */
+int corr_set_tiles(corr_t h, int window, int stages);
+
 /* Per-antenna corrections of Sec. 2.1.  gains: N complex values as 2N floats
  * (re, im); delays: N floats, in samples.  Either may be NULL (gain 1,
  * delay 0); both NULL switches corrections off.  Host or device memory; the

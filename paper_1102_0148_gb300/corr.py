@@ -37,6 +37,7 @@ _SIGS = {
     "corr_create": (_int, [ctypes.POINTER(_vp), _int, _int, _int]),
     "corr_set_stream": (_int, [_vp, _vp]),
     "corr_set_chunk": (_int, [_vp, _i64]),
+    "corr_set_tiles": (_int, [_vp, _int, _int]),
     "corr_set_corrections": (_int, [_vp, _vp, _vp]),
     "corr_push": (_int, [_vp, _vp, _i64]),
     "corr_dump": (_int, [_vp, _vp, ctypes.POINTER(_i64), _int]),
@@ -109,6 +110,10 @@ def corr_set_stream(h, stream):
 
 def corr_set_chunk(h, max_spectra):
     return _check(_lib.corr_set_chunk(h, int(max_spectra)), h)
+
+
+def corr_set_tiles(h, window=0, stages=0):
+    return _check(_lib.corr_set_tiles(h, int(window), int(stages)), h)
 
 
 def corr_set_corrections(h, gains=None, delays=None):

@@ -238,15 +238,20 @@ int run_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, double2* acc) {
 
     if (h->use_tc) {
         prof_begin(h);
-        bool direct = false;
-        int rc = tc_run(h->tc, S_pad, h->partial, acc, h->scale, h->status, h->stream, h->err,
-                        &direct);
+        TcRun run{};
+        run.S_pad = S_pad;
+        run.partial = h->partial;
+        run.acc = acc;
+        run.scale = h->scale;
+        run.status = h->status;
+        TcPlan* plans[1] = {h->tc};
+        int rc = tc_launch(plans, 1, &run, h->stream, h->err);
         if (rc != CORR_OK) return rc;
         prof_end(h, CORR_KERNEL_XENGINE);
-        if (!direct) {
+        if (!run.direct) {
             prof_begin(h);
-            CUDA_TRY(h, launch_reduce_partials(h->partial, tc_num_partials(h->tc, S_pad),
-                                               (int64_t)h->C * h->P, acc, h->stream));
+            CUDA_TRY(h, launch_reduce_partials(h->partial, run.n_split, (int64_t)h->C * h->P, acc,
+                                               h->stream));
             prof_end(h, CORR_KERNEL_REDUCE);
         }
     } else {
@@ -446,6 +451,12 @@ int corr_set_chunk(corr_t h, int64_t max_spectra) {
         return set_err(h, CORR_ESTATE, "chunk size can only change between integrations");
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return alloc_workspace(h, max_spectra);
+}
+
+int corr_set_tiles(corr_t h, int window, int stages) {
+    if (!h) return CORR_EINVAL;
+    if (!h->use_tc) return set_err(h, CORR_EINVAL, "tile choices apply to tensor-core handles");
+    return tc_set_tiles(h->tc, window, stages, h->err);
 }
 
 int corr_set_corrections(corr_t h, const float* gains, const float* delays) {

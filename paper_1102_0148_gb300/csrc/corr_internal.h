@@ -23,6 +23,16 @@ inline int spec_elem_bytes(int t) {
 }
 inline int spec_planes(int t) { return t == SPEC_F16X2 ? 2 : 1; }
 
+// Row of the corner-turned workspace holding plane (0 = Re, 1 = Im) of
+// antenna i.  Antennas are grouped in blocks of 64; block b occupies rows
+// 128 b .. 128 b + 2 nb - 1 as [Re of its nb antennas; Im of them], nb =
+// min(64, N - 64 b).  For N <= 64 this is [Re Y_0..Re Y_{N-1}; Im Y_0..].
+__host__ __device__ __forceinline__ int spec_row(int plane, int i, int N) {
+    const int b = i >> 6;
+    const int nb = (N - 64 * b) < 64 ? (N - 64 * b) : 64;
+    return 128 * b + plane * nb + (i & 63);
+}
+
 // Pre-scale of the two-plane FP16 split; keeps |x|/16 below the FP16 range
 // limit for every 4-bit input up to K = 4096 (|X| <= 8K) with |g| < 3.
 constexpr float kSplitScale = 0.0625f;

@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kThreads) fengine_generic(FengineArgs a, int F
             if (f >= nfr) continue;
             const int plane = row / C;
             const int k = row - plane * C;
-            const int64_t off = ((int64_t)k * 2 * a.N + plane * a.N + i) * a.ld + s0 + f;
+            const int64_t off = ((int64_t)k * 2 * a.N + spec_row(plane, i, a.N)) * a.ld + s0 + f;
             store_spec(a.spec, a.spec_type, off, stg[row * FT + f], a.plane_stride);
         }
     }
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(kF512Threads, 2) fengine_k512(FengineArgs a) {
         const int plane = row >> 8;
         const int k = row & 255;
         const float* src = stg + 4 * m * kStgRow + row;
-        const int64_t off = ((int64_t)k * 2 * a.N + plane * a.N + i) * a.ld + s0 + 4 * m;
+        const int64_t off = ((int64_t)k * 2 * a.N + spec_row(plane, i, a.N)) * a.ld + s0 + 4 * m;
         store4<OUT>(a.spec, off, a.plane_stride, src[0], src[kStgRow], src[2 * kStgRow],
                     src[3 * kStgRow]);
     }

@@ -51,8 +51,12 @@ __global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt) {
             const int r = e / kTS;
             const int c = e - r * kTS;
             const float v = base[(int64_t)r * a.ld + s0 + c];
-            const int plane = r >= N;
-            tile[(c * 2 + plane) * NB4 + (r - plane * N)] = v;
+            // row r -> (plane, antenna) under the 64-antenna block layout
+            const int b = r >> 7;
+            const int w = r & 127;
+            const int nbk = (N - 64 * b) < 64 ? (N - 64 * b) : 64;
+            const int plane = w >= nbk;
+            tile[(c * 2 + plane) * NB4 + 64 * b + w - plane * nbk] = v;
         }
         __syncthreads();
         if (active) {

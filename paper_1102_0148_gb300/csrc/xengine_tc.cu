@@ -4,30 +4,38 @@
 // accumulate), Sec. 4 (the cross-multiply dominates the load; the paper
 // converts the FFT output to a narrower type with prescaling before it).
 //
-// For one channel k the spectra of a pass form A = [Re Y_0..Re Y_{N-1};
-// Im Y_0..Im Y_{N-1}] (2N rows, spectra along the contraction axis), and the
-// real Gram matrix G = A A^T holds every product the visibilities need:
-//   Re V_ij = G[i][j] + G[N+i][N+j],   Im V_ij = G[N+i][j] - G[i][N+j].
-// G is a dense contraction: D[128 x Nn] += A_tile[128 x 16|32] * A_tile^T with
-// both MMA operands read from the *same* TMA-loaded shared-memory tile (rows
-// beyond 2N are zero-filled by TMA), FP32 accumulators in TMEM.
+// For one channel k the spectra of a pass form the real matrix A whose rows
+// are the real and imaginary parts of every antenna (spectra along the
+// contraction axis); the Gram matrix G = A A^T holds every product the
+// visibilities need.  Antennas come in blocks of 64 (rows [Re; Im] of the
+// block, 128 rows at most); for a pair of blocks (b1 <= b2) with local
+// antennas i' < nb1 and j' < nb2,
+//   Re V_ij = G[i'][j'] + G[nb1+i'][nb2+j'],   Im V_ij = G[nb1+i'][j'] - G[i'][nb2+j'].
+// Each block pair is a dense contraction D[128 x Nn] += A_b1[128 x 16|32] *
+// A_b2^T on the tensor cores, operands loaded by TMA (rows past the antenna
+// count are zero-filled), FP32 accumulators in TMEM.  For a diagonal pair
+// both operands are the same shared-memory tile.
 //
 // Precisions (operands in shared memory, K-major, 128-byte swizzle):
-//   mode 0 (FP32-accurate): two FP16 planes x/16 = hi + lo; two MMAs per
-//           k-step, Dhh += hi hi^T and Dhl += hi lo^T; the epilogue forms
-//           G = 256 (Dhh + Dhl + Dhl^T)  (the lo lo^T term is below 2^-22).
+//   mode 0 (FP32-accurate): two FP16 planes x/16 = hi + lo.  Diagonal pairs
+//           issue Dhh += hi hi^T and Dhl += hi lo^T and form
+//           G = 256 (Dhh + Dhl + Dhl^T); off-diagonal pairs issue hi hi^T,
+//           hi lo^T and lo hi^T into one accumulator (lo lo^T is below 2^-22).
 //   mode 1: one FP16 plane (pre-scaled per antenna and channel).
 //   mode 2: one FP8-E4M3 plane (pre-scaled), kind::f8f6f4.
 //
-// CTA = 10 warps, persistent over work items (channel, range of spectra):
+// One launch may serve several correlators ("modes") of different N and K
+// that share the precision: work items (mode, channel, block pair, range of
+// spectra) are enumerated mode by mode and dealt round-robin to persistent
+// CTAs of 10 warps:
 //   warp 0    TMA producer (one lane)     -> stage ring (full/empty mbarriers)
 //   warp 1    TMEM allocator + MMA issuer (one lane) -> two TMEM accumulator sets
 //   warps 2-9 epilogue: TMEM -> registers, summed over windows -> G in shared
-//             memory -> V -> partials
+//             memory -> V -> FP64 accumulator (or FP32 partials)
 // The tensor core's FP32 accumulation into TMEM is biased (it loses about one
 // unit in the last place per accumulate, always toward zero), so TMEM only
-// accumulates one window of kWindow spectra; the epilogue adds the windows
-// with round-to-nearest FP32 arithmetic.  The two accumulator sets let the
+// accumulates one window of W spectra; the epilogue adds the windows with
+// round-to-nearest FP32 arithmetic.  The two accumulator sets let the
 // epilogue drain window n while the MMAs fill window n+1.
 // Every mbarrier wait is bounded by a global-timer deadline; on expiry the
 // kernel records a status code, drains its own copies and MMAs, frees TMEM
@@ -37,37 +45,69 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <vector>
 
 namespace gbcorr {
 namespace {
 
-constexpr int kTcThreads = 320;   // producer, MMA, 8 epilogue warps
-constexpr int kWindow = 128;      // spectra per TMEM accumulation window
-constexpr int kRows = 128;          // MMA M = TMA box rows
+constexpr int kTcThreads = 320;     // producer, MMA, 8 epilogue warps
+constexpr int kRows = 128;          // MMA M = TMA box rows = one antenna block
 constexpr int kRowBytes = 128;      // one swizzle span per row
 constexpr int kTileBytes = kRows * kRowBytes;
 constexpr uint32_t kTmemCols = 512; // two accumulator sets of 256 columns
 constexpr int kStatusTimeout = 2;
+constexpr int kDefaultWindow = 128; // spectra per TMEM accumulation window
+
+struct TcModeArgs {
+    int N, C, P;
+    int nblk, npairs;         // antenna blocks of 64 and their pairs b1 <= b2
+    int n_split;
+    int item_base, n_items;   // items: channel fastest, then block pair, then split
+    int64_t S_pad, S_item;
+    float2* partial;          // [n_split][C][P] FP32 partials (acc == nullptr)
+    double2* acc;             // [C][P] FP64 accumulator, added to directly
+    const float* scale;       // [N][C] pre-cast scales (modes 1, 2)
+};
 
 struct TcArgs {
-    int N, C, R2, Nn, P;
-    int mode;                 // 0 split FP16 (two planes), 1 FP16, 2 FP8
-    int planes;
-    int stages;
-    int KT;                   // spectra per k-tile (one 128-byte row of operands)
-    int W;                    // spectra per TMEM accumulation window (multiple of KT)
-    int64_t S_pad;
-    int64_t S_item;           // spectra per work item (multiple of KT)
-    int n_items;              // C * n_split
-    uint32_t idesc;
-    float2* partial;          // [n_split][C][P]
-    double2* acc;             // [C][P] FP64 accumulator, used directly when n_split == 1
-    const float* scale;       // [N][C] (modes 1, 2)
+    CUtensorMap tmap[kMaxTcModes];
+    TcModeArgs md[kMaxTcModes];
+    int n_modes, total_items;
+    int stages, KT, W;
+    int two_tiles;            // stage slots hold separate A and B tiles
+    int gs_floats;            // epilogue G buffer (largest 2nb x (2nb + 1) of the modes)
     int* status;
     unsigned long long timeout_ns;
 };
+
+struct Item {
+    int m, k, b1, b2, sp;
+};
+
+__device__ __forceinline__ Item decode_item(const TcArgs& a, int g) {
+    int m = 0;
+    while (m + 1 < a.n_modes && g >= a.md[m + 1].item_base) ++m;
+    const TcModeArgs& d = a.md[m];
+    int l = g - d.item_base;
+    Item it;
+    it.m = m;
+    it.k = l % d.C;
+    l /= d.C;
+    int pr = l % d.npairs;
+    it.sp = l / d.npairs;
+    int b1 = 0;
+    while (pr >= d.nblk - b1) {
+        pr -= d.nblk - b1;
+        ++b1;
+    }
+    it.b1 = b1;
+    it.b2 = b1 + pr;
+    return it;
+}
+
+__device__ __forceinline__ int block_ants(int N, int b) { return min(64, N - 64 * b); }
 
 // ---------------------------------------------------------------- PTX helpers
 
@@ -178,16 +218,6 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-          "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-}
-
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
@@ -201,21 +231,21 @@ __device__ __forceinline__ void tmem_ld_wait() {
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
+
 // --------------------------------------------------------------------- kernel
 
 template <int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1)
-    xengine_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_constant__ TcArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     constexpr int planes = MODE == 0 ? 2 : 1;
-    constexpr uint32_t stage_bytes = planes * kTileBytes;
+    constexpr uint32_t tile_set = planes * kTileBytes;          // one operand, all planes
+    const uint32_t stage_bytes = tile_set * (a.two_tiles ? 2u : 1u);
     unsigned char* stages = smem;
-    const int ldg = a.R2 + 1;
-    float* Gs = reinterpret_cast<float*>(smem + a.stages * stage_bytes);
+    float* Gs = reinterpret_cast<float*>(smem + a.stages * stage_bytes);   // <= 128 x 129
     uint64_t* bars = reinterpret_cast<uint64_t*>(
-        (reinterpret_cast<uintptr_t>(Gs + a.R2 * ldg) + 15) & ~(uintptr_t)15);
+        (reinterpret_cast<uintptr_t>(Gs + a.gs_floats) + 15) & ~(uintptr_t)15);
     uint64_t* full = bars;
     uint64_t* empty = full + a.stages;
     uint64_t* accf = empty + a.stages;
@@ -261,11 +291,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             int armed_phase[16];
             for (int s = 0; s < 16; ++s) armed_phase[s] = -1;
             bool ok = true;
-            for (int item = blockIdx.x; ok && item < a.n_items; item += gridDim.x) {
-                const int k = item % a.C;
-                const int sp = item / a.C;
-                const int64_t s_beg = (int64_t)sp * a.S_item;
-                const int64_t s_end = min(a.S_pad, s_beg + a.S_item);
+            for (int g = blockIdx.x; ok && g < a.total_items; g += gridDim.x) {
+                const Item itm = decode_item(a, g);
+                const TcModeArgs& d = a.md[itm.m];
+                const CUtensorMap* map = &a.tmap[itm.m];
+                const bool diag = itm.b1 == itm.b2;
+                const uint32_t bytes = tile_set * (diag ? 1u : 2u);
+                const int ra = kRows * itm.b1;
+                const int rb = kRows * itm.b2;
+                const int64_t s_beg = (int64_t)itm.sp * d.S_item;
+                const int64_t s_end = min(d.S_pad, s_beg + d.S_item);
                 for (int64_t s = s_beg; s < s_end; s += a.KT, ++it) {
                     const uint32_t st = it % a.stages;
                     const uint32_t ph = (it / a.stages) & 1u;
@@ -274,10 +309,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         break;
                     }
                     const uint32_t fb = smem_u32(&full[st]);
-                    mbar_expect_tx(fb, stage_bytes);
+                    mbar_expect_tx(fb, bytes);
                     const uint32_t dst = smem_u32(stages + st * stage_bytes);
-                    tma_load_3d(dst, &tmap, fb, (int)s, 0, k);
-                    if (planes == 2) tma_load_3d(dst + kTileBytes, &tmap, fb, (int)s, 0, a.C + k);
+                    tma_load_3d(dst, map, fb, (int)s, ra, itm.k);
+                    if (planes == 2) tma_load_3d(dst + kTileBytes, map, fb, (int)s, ra, d.C + itm.k);
+                    if (!diag) {
+                        tma_load_3d(dst + tile_set, map, fb, (int)s, rb, itm.k);
+                        if (planes == 2)
+                            tma_load_3d(dst + tile_set + kTileBytes, map, fb, (int)s, rb, d.C + itm.k);
+                    }
                     armed_phase[st] = (int)ph;
                 }
             }
@@ -293,17 +333,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
     } else if (warp == 1) {
         // ------------------------------------------------------- MMA issuer
-        // One TMEM accumulation window = W spectra; windows alternate between
-        // the two accumulator sets so the epilogue drains one while the next fills.
         if (lane == 0) {
             uint32_t it = 0;
             int wi = 0;
             bool ok = true;
             bool issued = false;
-            for (int item = blockIdx.x; ok && item < a.n_items; item += gridDim.x) {
-                const int sp = item / a.C;
-                const int64_t s_beg = (int64_t)sp * a.S_item;
-                const int64_t s_end = min(a.S_pad, s_beg + a.S_item);
+            for (int g = blockIdx.x; ok && g < a.total_items; g += gridDim.x) {
+                const Item itm = decode_item(a, g);
+                const TcModeArgs& d = a.md[itm.m];
+                const bool diag = itm.b1 == itm.b2;
+                const int Nn = (2 * block_ants(d.N, itm.b2) + 15) & ~15;
+                // D = F32, A/B = F16 (kind::f16) or E4M3 (kind::f8f6f4), K-major,
+                // N>>3 at bits 17-22, M>>4 at bits 24-28
+                const uint32_t idesc =
+                    (1u << 4) | ((uint32_t)(Nn >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+                const int64_t s_beg = (int64_t)itm.sp * d.S_item;
+                const int64_t s_end = min(d.S_pad, s_beg + d.S_item);
                 for (int64_t w0 = s_beg; ok && w0 < s_end; w0 += a.W, ++wi) {
                     const int b = wi & 1;
                     const uint32_t aph = (uint32_t)(wi >> 1) & 1u;
@@ -312,8 +357,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t d_hh = tmem + (uint32_t)b * 256u;
-                    const uint32_t d_hl = d_hh + 128u;
+                    const uint32_t d0 = tmem + (uint32_t)b * 256u;
+                    const uint32_t d1 = d0 + 128u;
                     const int64_t w1 = min(s_end, w0 + a.W);
                     uint32_t acc = 0;
                     for (int64_t s = w0; s < w1; s += a.KT, ++it) {
@@ -327,11 +372,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         const uint32_t base = smem_u32(stages + st * stage_bytes);
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
-                            const uint64_t ad = sw128_desc(base + 32u * kk);
-                            mma<MODE>(d_hh, ad, ad, a.idesc, acc);
-                            if (planes == 2) {
-                                const uint64_t bd = sw128_desc(base + kTileBytes + 32u * kk);
-                                mma<MODE>(d_hl, ad, bd, a.idesc, acc);
+                            const uint64_t ah = sw128_desc(base + 32u * kk);
+                            if (MODE == 0) {
+                                const uint64_t al = sw128_desc(base + kTileBytes + 32u * kk);
+                                if (diag) {
+                                    mma<MODE>(d0, ah, ah, idesc, acc);
+                                    mma<MODE>(d1, ah, al, idesc, acc);
+                                } else {
+                                    const uint64_t bh = sw128_desc(base + tile_set + 32u * kk);
+                                    const uint64_t bl = sw128_desc(base + tile_set + kTileBytes + 32u * kk);
+                                    mma<MODE>(d0, ah, bh, idesc, acc);
+                                    mma<MODE>(d0, ah, bl, idesc, 1u);
+                                    mma<MODE>(d0, al, bh, idesc, 1u);
+                                }
+                            } else {
+                                const uint64_t bd = diag ? ah : sw128_desc(base + tile_set + 32u * kk);
+                                mma<MODE>(d0, ah, bd, idesc, acc);
                             }
                             acc = 1;
                         }
@@ -352,29 +408,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
     } else {
         // --------------------------------------------------------- epilogue
-        // 8 warps: warp w reads TMEM lane quadrant w % 4 (rows 32q..32q+31) and
-        // one half of the Nn accumulator columns.  Windows are summed in
-        // registers with round-to-nearest FP32 adds (the tensor core's own
-        // accumulation is only trusted over one short window).
+        // 8 warps: warp w reads TMEM lane quadrant w % 4 (rows 32q..32q+31)
+        // and one half of the Nn accumulator columns.
         const int et = threadIdx.x - 64;            // 0..255
         const int q = warp & 3;
         const int h = (warp - 2) >> 2;
         const int r = 32 * q + lane;
-        const int NH = a.Nn >> 1;                   // columns per half, multiple of 8
-        const int col0 = h * NH;
-        const int N = a.N, R2 = a.R2, C = a.C, P = a.P;
         int wi = 0;
         bool ok = true;
-        for (int item = blockIdx.x; ok && item < a.n_items; item += gridDim.x) {
-            const int k = item % C;
-            const int sp = item / C;
-            const int64_t s_beg = (int64_t)sp * a.S_item;
-            const int64_t s_end = min(a.S_pad, s_beg + a.S_item);
-            float g[64], t[64];
+        for (int g = blockIdx.x; ok && g < a.total_items; g += gridDim.x) {
+            const Item itm = decode_item(a, g);
+            const TcModeArgs& d = a.md[itm.m];
+            const bool diag = itm.b1 == itm.b2;
+            const bool use_t = MODE == 0 && diag;
+            const int nb1 = block_ants(d.N, itm.b1);
+            const int nb2 = block_ants(d.N, itm.b2);
+            const int R2a = 2 * nb1;
+            const int R2b = 2 * nb2;
+            const int NH = ((R2b + 15) & ~15) >> 1;  // columns per half, multiple of 8
+            const int col0 = h * NH;
+            const int64_t s_beg = (int64_t)itm.sp * d.S_item;
+            const int64_t s_end = min(d.S_pad, s_beg + d.S_item);
+            float gacc[64], tacc[64];
 #pragma unroll
             for (int j = 0; j < 64; ++j) {
-                g[j] = 0.f;
-                t[j] = 0.f;
+                gacc[j] = 0.f;
+                tacc[j] = 0.f;
             }
             for (int64_t w0 = s_beg; w0 < s_end; w0 += a.W, ++wi) {
                 const int b = wi & 1;
@@ -393,20 +452,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (8 * c < NH) {
                         uint32_t v[8];
                         tmem_ld8(trow + 8u * c, v);
-                        if (planes == 2) {
+                        if (use_t) {
                             uint32_t w[8];
                             tmem_ld8(trow + 128u + 8u * c, w);
                             tmem_ld_wait();
 #pragma unroll
                             for (int j = 0; j < 8; ++j) {
                                 const float wf = __uint_as_float(w[j]);
-                                g[8 * c + j] += __uint_as_float(v[j]) + wf;
-                                t[8 * c + j] += wf;
+                                gacc[8 * c + j] += __uint_as_float(v[j]) + wf;
+                                tacc[8 * c + j] += wf;
                             }
                         } else {
                             tmem_ld_wait();
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) g[8 * c + j] += __uint_as_float(v[j]);
+                            for (int j = 0; j < 8; ++j) gacc[8 * c + j] += __uint_as_float(v[j]);
                         }
                     }
                 }
@@ -414,52 +473,63 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 mbar_arrive(smem_u32(&acce[b]));   // this TMEM set may be refilled now
             }
             if (!ok) break;
-            if (r < R2) {
+            const int ldg = R2b + 1;
+            if (r < R2a) {
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int col = col0 + 8 * c + j;
-                        if (8 * c < NH && col < R2) Gs[r * ldg + col] = g[8 * c + j];
+                        if (8 * c < NH && col < R2b) Gs[r * ldg + col] = gacc[8 * c + j];
                     }
             }
             epi_sync();
-            if (planes == 2) {
+            if (use_t) {
                 // G[col][r] += Dhl[r][col]: each element is touched by one thread here
-                if (r < R2) {
+                if (r < R2a) {
 #pragma unroll
                     for (int c = 0; c < 8; ++c)
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
                             const int col = col0 + 8 * c + j;
-                            if (8 * c < NH && col < R2) Gs[col * ldg + r] += t[8 * c + j];
+                            if (8 * c < NH && col < R2b) Gs[col * ldg + r] += tacc[8 * c + j];
                         }
                 }
                 epi_sync();
             }
             const float gs = MODE == 0 ? 1.0f / (kSplitScale * kSplitScale) : 1.0f;
-            float2* out = a.partial + ((int64_t)sp * C + k) * P;
-            int i = 0;
-            int row_next = N;                       // first p of row i + 1
-            for (int p = et; p < P; p += 256) {
-                while (p >= row_next) {
-                    ++i;
-                    row_next += N - i;
+            const int N = d.N, C = d.C, P = d.P;
+            const int npl = diag ? nb1 * (nb1 + 1) / 2 : nb1 * nb2;
+            int li = 0;
+            int row_next = nb1;                     // triangle: first index of row li + 1
+            for (int pl = et; pl < npl; pl += 256) {
+                int lj;
+                if (diag) {
+                    while (pl >= row_next) {
+                        ++li;
+                        row_next += nb1 - li;
+                    }
+                    lj = li + (pl - (row_next - (nb1 - li)));
+                } else {
+                    li = pl / nb2;
+                    lj = pl - li * nb2;
                 }
-                const int j = i + (p - (row_next - (N - i)));
-                const float re = Gs[i * ldg + j] + Gs[(N + i) * ldg + N + j];
-                const float im = Gs[(N + i) * ldg + j] - Gs[i * ldg + N + j];
+                const float re = Gs[li * ldg + lj] + Gs[(nb1 + li) * ldg + nb2 + lj];
+                const float im = Gs[(nb1 + li) * ldg + lj] - Gs[li * ldg + nb2 + lj];
+                const int i = 64 * itm.b1 + li;
+                const int j = 64 * itm.b2 + lj;
+                const int p = i * N - i * (i - 1) / 2 + (j - i);
                 float f = gs;
                 if (MODE != 0)
-                    f = 1.0f / (__ldg(a.scale + (int64_t)i * C + k) * __ldg(a.scale + (int64_t)j * C + k));
-                if (a.acc) {
-                    double2* d = a.acc + (int64_t)k * P + p;   // sole owner of (k, p) here
-                    double2 v = *d;
+                    f = 1.0f / (__ldg(d.scale + (int64_t)i * C + itm.k) * __ldg(d.scale + (int64_t)j * C + itm.k));
+                if (d.acc) {
+                    double2* dst = d.acc + (int64_t)itm.k * P + p;   // sole owner of (k, p) here
+                    double2 v = *dst;
                     v.x += (double)(re * f);
                     v.y += (double)(im * f);
-                    *d = v;
+                    *dst = v;
                 } else {
-                    out[p] = make_float2(re * f, im * f);
+                    d.partial[((int64_t)itm.sp * C + itm.k) * P + p] = make_float2(re * f, im * f);
                 }
             }
             epi_sync();
@@ -479,13 +549,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // ----------------------------------------------------------------- host side
 
-constexpr uint32_t make_idesc(int M, int Nn) {
-    // D = F32 (bits 4-5); A, B = F16 for kind::f16 and E4M3 for kind::f8f6f4
-    // (format code 0 in both, bits 7-9 / 10-12); both K-major; N>>3 at
-    // bits 17-22; M>>4 at bits 24-28.
-    return (1u << 4) | ((uint32_t)(Nn >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -501,27 +564,27 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
     return fn;
 }
 
+constexpr size_t kSmemBudget = 227 * 1024;
+
 }  // namespace
 
 struct TcPlan {
-    int N = 0, C = 0, R2 = 0, Nn = 0, P = 0;
-    int mode = 0, planes = 1, stages = 4, KT = 64;
+    int N = 0, C = 0, P = 0, nblk = 1, npairs = 1;
+    int mode = 0, planes = 1, KT = 64;
     int num_sms = 0;
-    size_t smem_bytes = 0;
     CUtensorMap tmap;
     bool have_map = false;
     int64_t cap = 0;
     int max_split = 1;
-    int last_split = 1;
+    int window = 0;           // 0 = kDefaultWindow
+    int stages = 0;           // 0 = as many as shared memory allows
     unsigned long long timeout_ns = 4000000000ull;
+    // split decisions already made, keyed by the S_pad of every mode in the launch
+    std::vector<std::pair<std::vector<int64_t>, std::vector<int>>> split_cache;
 };
 
 int tc_plan_create(TcPlan** out, int N, int C, int spec_type, std::string& err) {
     *out = nullptr;
-    if (2 * N > kRows) {
-        err = "tensor-core X-engine handles N <= 64 antennas; use CORR_FP32_SIMT for larger N";
-        return CORR_EUNSUPPORTED;
-    }
     if (!get_encoder()) {
         err = "cuTensorMapEncodeTiled is not available from the driver";
         return CORR_ECUDA;
@@ -529,43 +592,17 @@ int tc_plan_create(TcPlan** out, int N, int C, int spec_type, std::string& err) 
     TcPlan* p = new TcPlan();
     p->N = N;
     p->C = C;
-    p->R2 = 2 * N;
-    p->Nn = (2 * N + 15) / 16 * 16;
     p->P = N * (N + 1) / 2;
+    p->nblk = (N + 63) / 64;
+    p->npairs = p->nblk * (p->nblk + 1) / 2;
     p->mode = spec_type == SPEC_F16X2 ? 0 : (spec_type == SPEC_F16 ? 1 : 2);
     p->planes = p->mode == 0 ? 2 : 1;
     p->KT = p->mode == 2 ? 128 : 64;
-    const size_t stage_bytes = (size_t)p->planes * kTileBytes;
-    const size_t gs_bytes = (size_t)p->R2 * (p->R2 + 1) * sizeof(float);
-    const size_t budget = 227 * 1024 - 1024 - 256 - gs_bytes;
-    p->stages = (int)(budget / stage_bytes);
-    if (p->stages > 8) p->stages = 8;
-    if (p->stages < 2) {
-        delete p;
-        err = "shared memory too small for the tensor-core X-engine";
-        return CORR_EUNSUPPORTED;
-    }
-    p->smem_bytes = 1024 + p->stages * stage_bytes + gs_bytes + 16 + (2 * p->stages + 5) * 8 + 16;
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         delete p;
         err = "cudaDeviceGetAttribute failed";
-        return CORR_ECUDA;
-    }
-    cudaError_t e = cudaSuccess;
-    if (p->mode == 0)
-        e = cudaFuncSetAttribute(xengine_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)p->smem_bytes);
-    else if (p->mode == 1)
-        e = cudaFuncSetAttribute(xengine_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)p->smem_bytes);
-    else
-        e = cudaFuncSetAttribute(xengine_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)p->smem_bytes);
-    if (e != cudaSuccess) {
-        delete p;
-        err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
         return CORR_ECUDA;
     }
     *out = p;
@@ -577,8 +614,9 @@ int tc_plan_update(TcPlan* p, void* spec, int64_t cap, int N, int C, int spec_ty
     (void)N;
     (void)C;
     const int eb = spec_elem_bytes(spec_type);
-    cuuint64_t dims[3] = {(cuuint64_t)cap, (cuuint64_t)p->R2, (cuuint64_t)p->planes * p->C};
-    cuuint64_t strides[2] = {(cuuint64_t)cap * eb, (cuuint64_t)p->R2 * cap * eb};
+    const int R2 = 2 * p->N;
+    cuuint64_t dims[3] = {(cuuint64_t)cap, (cuuint64_t)R2, (cuuint64_t)p->planes * p->C};
+    cuuint64_t strides[2] = {(cuuint64_t)cap * eb, (cuuint64_t)R2 * cap * eb};
     cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / eb), (cuuint32_t)kRows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt =
@@ -594,83 +632,179 @@ int tc_plan_update(TcPlan* p, void* spec, int64_t cap, int N, int C, int spec_ty
     }
     p->have_map = true;
     p->cap = cap;
-    p->max_split = (int)((cap + 255) / 256);
+    p->max_split = (int)std::min<int64_t>(8, (cap + 255) / 256);
+    p->split_cache.clear();
     return CORR_OK;
 }
 
-// Split of the spectra range that balances whole k-tiles over the SMs.
-static void choose_split(const TcPlan* p, int64_t S_pad, int& n_split, int64_t& S_item) {
-    const int64_t tiles = S_pad / p->KT;
-    double best = -1.0;
-    n_split = 1;
-    S_item = S_pad;
-    for (int n = 1; n <= p->max_split && n <= tiles; ++n) {
-        const int64_t per = (tiles + n - 1) / n;              // k-tiles per item
-        const int nn = (int)((tiles + per - 1) / per);        // items per channel
-        const int64_t items = (int64_t)p->C * nn;
-        // round-robin over the SMs: the busiest SM does ceil(items/SMs) items
-        const int64_t rounds = (items + p->num_sms - 1) / p->num_sms;
-        const double work = (double)rounds * (double)(per + 2);   // +2: per-item overhead
-        const double eff = (double)(tiles * p->C) / ((double)p->num_sms * work);
-        const double bonus = nn == 1 ? 1.15 : 1.0;   // n = 1 needs no reduction launch
-        if (eff * bonus > best + 1e-9) {
-            best = eff * bonus;
-            n_split = nn;
-            S_item = per * p->KT;
+int tc_set_tiles(TcPlan* p, int window, int stages, std::string& err) {
+    if (window != 0 && (window < p->KT || window % p->KT || window > 4096)) {
+        err = "window must be a multiple of the k-tile (64 spectra, 128 for FP8) up to 4096";
+        return CORR_EINVAL;
+    }
+    if (stages != 0 && (stages < 2 || stages > 16)) {
+        err = "stages must be in [2, 16]";
+        return CORR_EINVAL;
+    }
+    p->window = window;
+    p->stages = stages;
+    return CORR_OK;
+}
+
+namespace {
+
+struct LaunchShape {
+    int two_tiles, gs_floats, stages, W;
+    size_t smem;
+};
+
+LaunchShape launch_shape(TcPlan* const* plans, int n) {
+    LaunchShape L{};
+    int r2max = 0;
+    for (int m = 0; m < n; ++m) {
+        L.two_tiles |= plans[m]->nblk > 1;
+        r2max = std::max(r2max, 2 * std::min(64, plans[m]->N));
+    }
+    L.gs_floats = r2max * (r2max + 1);
+    const size_t stage_bytes = (size_t)plans[0]->planes * kTileBytes * (L.two_tiles ? 2 : 1);
+    const size_t fixed = 1024 + (size_t)L.gs_floats * 4 + 16 + 16 + 8 * (2 * 16 + 5);
+    int smax = (int)((kSmemBudget - fixed) / stage_bytes);
+    smax = std::min(smax, 16);
+    L.stages = plans[0]->stages ? std::min(plans[0]->stages, smax) : std::min(smax, 8);
+    L.W = plans[0]->window ? plans[0]->window : std::max(kDefaultWindow, plans[0]->KT);
+    L.smem = fixed + (size_t)L.stages * stage_bytes;
+    return L;
+}
+
+// Work-list split: every mode's pass of S_pad frames is cut into n_split
+// ranges of whole k-tiles.  The choice minimises the busiest CTA's work under
+// the kernel's round-robin deal, preferring one range per channel (the
+// epilogue then accumulates in FP64 directly and no reduction is launched).
+std::vector<int> choose_splits(TcPlan* const* plans, int n, const int64_t* S_pad) {
+    std::vector<int64_t> key(S_pad, S_pad + n);
+    auto& cache = plans[0]->split_cache;
+    for (auto& e : cache)
+        if (e.first == key) return e.second;
+    const int sms = plans[0]->num_sms;
+    int64_t max_tiles = 1;
+    for (int m = 0; m < n; ++m) max_tiles = std::max<int64_t>(max_tiles, S_pad[m] / plans[m]->KT);
+    std::vector<int> best(n, 1);
+    double best_score = 1e300;
+    std::vector<double> load(sms);
+    for (int64_t T = 1; T <= max_tiles * 2; T *= 2) {
+        std::vector<int> sp(n);
+        bool needs_reduce = false;
+        for (int m = 0; m < n; ++m) {
+            const int64_t tiles = std::max<int64_t>(1, S_pad[m] / plans[m]->KT);
+            int64_t ns = (tiles + T - 1) / T;
+            ns = std::min<int64_t>(ns, plans[m]->max_split);
+            const int64_t per = (tiles + ns - 1) / ns;
+            sp[m] = (int)((tiles + per - 1) / per);
+            needs_reduce |= sp[m] > 1;
+        }
+        std::fill(load.begin(), load.end(), 0.0);
+        int64_t g = 0;
+        for (int m = 0; m < n; ++m) {
+            const TcPlan* p = plans[m];
+            const int64_t tiles = std::max<int64_t>(1, S_pad[m] / p->KT);
+            const int64_t per = (tiles + sp[m] - 1) / sp[m];
+            for (int s = 0; s < sp[m]; ++s) {
+                const int64_t t = std::min<int64_t>(per, tiles - (int64_t)s * per);
+                for (int pr = 0; pr < p->npairs; ++pr) {
+                    const double w = (double)t * (p->nblk > 1 ? 1.5 : 1.0) + 2.0;
+                    for (int k = 0; k < p->C; ++k, ++g) load[g % sms] += w;
+                }
+            }
+        }
+        double score = *std::max_element(load.begin(), load.end());
+        if (needs_reduce) score *= 1.15;
+        if (score < best_score - 1e-9) {
+            best_score = score;
+            best = sp;
         }
     }
+    cache.emplace_back(key, best);
+    if (cache.size() > 16) cache.erase(cache.begin());
+    return best;
 }
 
-int tc_num_partials(const TcPlan* p, int64_t S_pad) {
-    int n;
-    int64_t si;
-    choose_split(p, S_pad, n, si);
-    return n;
-}
+}  // namespace
 
-int tc_run(TcPlan* p, int64_t S_pad, float2* partial, double2* acc, const float* scale,
-           int* status, cudaStream_t st, std::string& err, bool* direct) {
-    *direct = false;
-    if (!p->have_map) {
-        err = "tensor-core plan has no workspace";
-        return CORR_ESTATE;
+int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::string& err) {
+    if (n < 1 || n > kMaxTcModes) {
+        err = "between 1 and 4 modes per tensor-core launch";
+        return CORR_EINVAL;
     }
-    if (S_pad <= 0) return CORR_OK;
-    TcArgs a{};
-    a.N = p->N;
-    a.C = p->C;
-    a.R2 = p->R2;
-    a.Nn = p->Nn;
-    a.P = p->P;
-    a.mode = p->mode;
-    a.planes = p->planes;
-    a.stages = p->stages;
-    a.KT = p->KT;
-    a.W = kWindow;
-    a.S_pad = S_pad;
-    int n_split;
-    choose_split(p, S_pad, n_split, a.S_item);
-    a.n_items = p->C * n_split;
-    a.idesc = make_idesc(kRows, p->Nn);
-    a.partial = partial;
-    a.acc = (n_split == 1) ? acc : nullptr;
-    a.scale = scale;
-    a.status = status;
-    a.timeout_ns = p->timeout_ns;
-    const int grid = a.n_items < p->num_sms ? a.n_items : p->num_sms;
-    if (p->mode == 0)
-        xengine_tc_kernel<0><<<grid, kTcThreads, p->smem_bytes, st>>>(p->tmap, a);
-    else if (p->mode == 1)
-        xengine_tc_kernel<1><<<grid, kTcThreads, p->smem_bytes, st>>>(p->tmap, a);
-    else
-        xengine_tc_kernel<2><<<grid, kTcThreads, p->smem_bytes, st>>>(p->tmap, a);
-    cudaError_t e = cudaGetLastError();
+    for (int m = 0; m < n; ++m) {
+        if (!plans[m]->have_map) {
+            err = "tensor-core plan has no workspace";
+            return CORR_ESTATE;
+        }
+        if (plans[m]->mode != plans[0]->mode) {
+            err = "modes of one tensor-core launch must share the X-engine precision";
+            return CORR_EINVAL;
+        }
+    }
+    std::vector<int64_t> S(n);
+    for (int m = 0; m < n; ++m) S[m] = runs[m].S_pad;
+    const std::vector<int> sp = choose_splits(plans, n, S.data());
+    const LaunchShape L = launch_shape(plans, n);
+    TcArgs a;
+    memset(&a, 0, sizeof a);
+    a.n_modes = n;
+    a.stages = L.stages;
+    a.KT = plans[0]->KT;
+    a.W = L.W;
+    a.two_tiles = L.two_tiles;
+    a.gs_floats = L.gs_floats;
+    a.status = runs[0].status;
+    a.timeout_ns = plans[0]->timeout_ns;
+    int base = 0;
+    for (int m = 0; m < n; ++m) {
+        const TcPlan* p = plans[m];
+        a.tmap[m] = p->tmap;
+        TcModeArgs& d = a.md[m];
+        d.N = p->N;
+        d.C = p->C;
+        d.P = p->P;
+        d.nblk = p->nblk;
+        d.npairs = p->npairs;
+        d.S_pad = runs[m].S_pad;
+        const int64_t tiles = std::max<int64_t>(1, d.S_pad / p->KT);
+        const int64_t per = (tiles + sp[m] - 1) / sp[m];
+        d.S_item = per * p->KT;
+        d.n_split = d.S_pad > 0 ? (int)((d.S_pad + d.S_item - 1) / d.S_item) : 0;
+        d.item_base = base;
+        d.n_items = d.n_split * p->npairs * p->C;
+        base += d.n_items;
+        d.partial = runs[m].partial;
+        d.acc = d.n_split == 1 ? runs[m].acc : nullptr;
+        d.scale = runs[m].scale;
+        runs[m].n_split = d.n_split;
+        runs[m].direct = d.acc != nullptr || d.n_split == 0;
+    }
+    a.total_items = base;
+    if (base == 0) return CORR_OK;
+    const int grid = std::min(base, plans[0]->num_sms);
+    cudaError_t e;
+    if (plans[0]->mode == 0) {
+        e = cudaFuncSetAttribute(xengine_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)L.smem);
+        if (e == cudaSuccess) xengine_tc_kernel<0><<<grid, kTcThreads, L.smem, st>>>(a);
+    } else if (plans[0]->mode == 1) {
+        e = cudaFuncSetAttribute(xengine_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)L.smem);
+        if (e == cudaSuccess) xengine_tc_kernel<1><<<grid, kTcThreads, L.smem, st>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(xengine_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)L.smem);
+        if (e == cudaSuccess) xengine_tc_kernel<2><<<grid, kTcThreads, L.smem, st>>>(a);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = std::string("tensor-core X-engine launch: ") + cudaGetErrorString(e);
         return CORR_ECUDA;
     }
-    p->last_split = n_split;
-    *direct = a.acc != nullptr;
     return CORR_OK;
 }
 

@@ -7,19 +7,32 @@
 
 namespace gbcorr {
 
+constexpr int kMaxTcModes = 4;
+
 struct TcPlan;
+
+// What one mode of a tensor-core launch reads and writes.
+struct TcRun {
+    int64_t S_pad;            // frames in the workspace pass (multiple of 128)
+    float2* partial;          // [max_split][C][P] partials, used when n_split > 1
+    double2* acc;             // [C][P] FP64 accumulator, added to when n_split == 1
+    const float* scale;       // [N][C] pre-cast scales (FP16 / FP8), else nullptr
+    int* status;              // device status word (bounded waits)
+    int n_split;              // out: ranges per channel
+    bool direct;              // out: accumulated into acc (no reduction needed)
+};
 
 // Prepare a plan for N antennas and C channels of workspace type spec_type.
 int tc_plan_create(TcPlan** out, int N, int C, int spec_type, std::string& err);
 // (Re)bind the plan to a workspace of `cap` frames per row.
 int tc_plan_update(TcPlan* p, void* spec, int64_t cap, int N, int C, int spec_type, std::string& err);
-// Run the X-engine over S_pad frames.  When the pass is one work item per
-// channel the epilogue adds V straight into the FP64 accumulator `acc`
-// ([C][P]) and *direct is set; otherwise it writes tc_num_partials() partial
-// blocks of [C][P] complex64 to `partial` for the reduction kernel.
-int tc_run(TcPlan* p, int64_t S_pad, float2* partial, double2* acc, const float* scale,
-           int* status, cudaStream_t st, std::string& err, bool* direct);
-int tc_num_partials(const TcPlan* p, int64_t S_pad);
+// Tile choices: TMEM accumulation window (spectra, 0 = default) and
+// pipeline stages (0 = as many as shared memory holds, up to 8).
+int tc_set_tiles(TcPlan* p, int window, int stages, std::string& err);
+// One persistent launch over the passes of n plans sharing a precision.
+// Modes whose run reports direct = false need the reduction of their
+// n_split partial blocks into acc.
+int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::string& err);
 void tc_plan_destroy(TcPlan* p);
 
 }  // namespace gbcorr

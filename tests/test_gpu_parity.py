@@ -132,10 +132,8 @@ def test_ragged_pushes_chunks_and_corrections(lib, torch_cuda, dtype):
 
 @pytest.mark.parametrize("dtype", DTYPES_FP32)
 @pytest.mark.parametrize("N,K,S", [(1, 16, 7), (2, 32, 1), (13, 128, 129), (64, 256, 200),
-                                   (65, 64, 50)])
+                                   (65, 64, 50), (128, 32, 70), (200, 16, 40)])
 def test_edge_shapes(lib, torch_cuda, dtype, N, K, S):
-    if dtype != "fp32_simt" and 2 * N > 128:
-        pytest.skip("the tensor-core X-engine tiles one 128-row block (N <= 64)")
     packed, _ = synth.make_samples(N, S * K, K, seed=SEED + N * 1000 + K)
     R, _ = oracle.correlate(packed, N, K)
     V, n = run_gpu(lib, torch_cuda, packed, N, K, dtype)
@@ -232,3 +230,27 @@ def test_precision_forms_cfg1(lib, torch_cuda, dtype):
     e = vis_error(V, R, N)
     print(f"{dtype}: normalised error vs FP64 oracle {e:.3g}")
     assert e <= PRECISION_BOUND[dtype], e
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "fp32_simt"])
+def test_n256_k1024(lib, torch_cuda, dtype):
+    """The density scale-up geometry: 256 antennas (four 64-antenna blocks,
+    ten block pairs per channel), K = 1024."""
+    N, K, S = 256, 1024, 160
+    packed, _ = synth.make_samples(N, S * K, K, seed=SEED + 256)
+    R, _ = oracle.correlate(packed, N, K)
+    V, n = run_gpu(lib, torch_cuda, packed, N, K, dtype)
+    assert n == S
+    assert vis_error(V, R, N) <= TOL
+
+
+@pytest.mark.parametrize("window,stages", [(64, 2), (256, 3), (512, 0)])
+def test_tile_choices_keep_parity(lib, torch_cuda, window, stages):
+    N, K, S = 44, 512, 600
+    packed, _ = synth.make_samples(N, S * K, K, seed=SEED + 21)
+    R, _ = oracle.correlate(packed, N, K)
+    with lib.Correlator(N, K, "fp32") as c:
+        lib.corr_set_tiles(c.h, window, stages)
+        c.push(torch_cuda.from_numpy(packed.reshape(-1)).cuda(), S * K)
+        V, n = c.dump(fp64=True)
+    assert vis_error(V, R, N) <= TOL

@@ -198,6 +198,52 @@ int corr_profile_read(corr_t h, int64_t* launches, double* ms, int n);
  * n/K must not exceed the chunk size.  Synchronises the handle's stream. */
 int corr_debug_spectra(corr_t h, const uint8_t* samples, int64_t n, float* spectra);
 
+/* ------------------------------------------------------------------------
+ * Batches: several correlators ("modes", e.g. sub-arrays with different N
+ * and K) whose X-engine work runs as ONE persistent tensor-core launch per
+ * pass (SURVEY's batching form; the paper's correlator serves one mode).
+ * All modes share the X-engine precision (CORR_FP32, CORR_FP16 or
+ * CORR_FP8E4M3) and one non-blocking stream owned by the batch; each mode
+ * keeps its own workspace and FP64 accumulators.  Per pass index the
+ * F-engine of every mode that has that pass is queued, then one launch
+ * covers all of their X-engine work.  With each mode's chunk at least its
+ * push size (corr_batch_set_chunk), a push is exactly one X-engine launch.
+ *
+ * corr_batch_create  n_modes in [1, 4]; N[m], K[m] as corr_create.
+ * corr_batch_push    samples[m]: device buffer of n[m] samples per antenna of
+ *                    mode m (layout as corr_push); n[m] may be 0.
+ * corr_batch_dump    vis[m] as corr_dump (host or device); n_spec may be NULL.
+ * corr_batch_capture one push of these device buffers plus a dump into the
+ *                    device buffers vis[m], run once eagerly and then
+ *                    recorded as a CUDA graph; the buffers' contents may
+ *                    change between replays, their addresses may not.
+ * corr_batch_replay  launch the recorded graph (asynchronous): every replay
+ *                    writes one complete integration per mode into vis[m];
+ *                    n_spec[m] (may be NULL) receives the spectra per mode.
+ * corr_batch_sync    wait for the batch stream; reports device-side errors.
+ * corr_batch_handle  the corr_t of mode m (corrections, scales, profiling;
+ *                    not to be destroyed or given another stream).
+ * corr_batch_get_stream  the batch's cudaStream_t.
+ * corr_batch_set_chunk / corr_batch_set_tiles  as corr_set_chunk /
+ *                    corr_set_tiles for every mode; discard a recorded graph.
+ * Errors: as the single-mode calls; corr_batch_last_error(b) has the message
+ * (corr_last_error(NULL) for corr_batch_create). */
+typedef struct corr_batch_s* corr_batch_t;
+
+int corr_batch_create(corr_batch_t* out, int n_modes, const int* N, const int* K, int dtype);
+int corr_batch_set_chunk(corr_batch_t b, int64_t max_spectra);
+int corr_batch_set_tiles(corr_batch_t b, int window, int stages);
+int corr_batch_push(corr_batch_t b, const uint8_t* const* samples, const int64_t* n);
+int corr_batch_dump(corr_batch_t b, void* const* vis, int64_t* n_spec, int vis_fp64);
+int corr_batch_capture(corr_batch_t b, const uint8_t* const* samples, const int64_t* n,
+                       void* const* vis, int vis_fp64);
+int corr_batch_replay(corr_batch_t b, int64_t* n_spec);
+int corr_batch_sync(corr_batch_t b);
+int corr_batch_handle(corr_batch_t b, int mode, corr_t* out);
+int corr_batch_get_stream(corr_batch_t b, void** stream);
+void corr_batch_destroy(corr_batch_t b);
+const char* corr_batch_last_error(corr_batch_t b);
+
 /* One-shot correlation that allocates no memory (the paper has no
  * counterpart; it exists for callers that must not allocate: a real-time
  * acquisition loop in which cudaMalloc/cudaFree could synchronise the device

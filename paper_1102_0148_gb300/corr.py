@@ -50,6 +50,18 @@ _SIGS = {
     "corr_debug_spectra": (_int, [_vp, _vp, _i64, _vp]),
     "corr_correlate_noalloc": (_int, [_vp, _i64, _int, _int, _vp, _vp]),
     "corr_set_scales": (_int, [_vp, _vp]),
+    "corr_batch_create": (_int, [ctypes.POINTER(_vp), _int, ctypes.POINTER(_int), ctypes.POINTER(_int), _int]),
+    "corr_batch_set_chunk": (_int, [_vp, _i64]),
+    "corr_batch_set_tiles": (_int, [_vp, _int, _int]),
+    "corr_batch_push": (_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i64)]),
+    "corr_batch_dump": (_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i64), _int]),
+    "corr_batch_capture": (_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.POINTER(_vp), _int]),
+    "corr_batch_replay": (_int, [_vp, ctypes.POINTER(_i64)]),
+    "corr_batch_sync": (_int, [_vp]),
+    "corr_batch_handle": (_int, [_vp, _int, ctypes.POINTER(_vp)]),
+    "corr_batch_get_stream": (_int, [_vp, ctypes.POINTER(_vp)]),
+    "corr_batch_destroy": (None, [_vp]),
+    "corr_batch_last_error": (ctypes.c_char_p, [_vp]),
     "corr_grad": (_int, [_vp, _vp, _i64, _vp, _vp, _vp, _int, _vp, _vp]),
     "corr_get_scales": (_int, [_vp, _vp]),
 }
@@ -195,6 +207,80 @@ def corr_correlate_noalloc(samples, n, N, K, vis, stream=None):
                   None)
 
 
+def _bcheck(rc, b):
+    if rc != CORR_OK:
+        m = _lib.corr_batch_last_error(b)
+        raise CorrError(rc, m.decode() if m else "")
+    return rc
+
+
+def _ptrs(bufs):
+    return (_vp * len(bufs))(*[_addr(x) for x in bufs])
+
+
+def corr_batch_create(N, K, dtype=CORR_FP32):
+    b = _vp()
+    n = len(N)
+    dtype = DTYPES.get(dtype, dtype) if isinstance(dtype, str) else dtype
+    rc = _lib.corr_batch_create(ctypes.byref(b), n, (_int * n)(*N), (_int * n)(*K), int(dtype))
+    _check(rc, None)
+    return b
+
+
+def corr_batch_set_chunk(b, max_spectra):
+    return _bcheck(_lib.corr_batch_set_chunk(b, int(max_spectra)), b)
+
+
+def corr_batch_set_tiles(b, window=0, stages=0):
+    return _bcheck(_lib.corr_batch_set_tiles(b, int(window), int(stages)), b)
+
+
+def corr_batch_push(b, samples, n):
+    return _bcheck(_lib.corr_batch_push(b, _ptrs(samples), (_i64 * len(n))(*n)), b)
+
+
+def corr_batch_dump(b, vis, fp64=False):
+    ns = (_i64 * len(vis))()
+    _bcheck(_lib.corr_batch_dump(b, _ptrs(vis), ns, 1 if fp64 else 0), b)
+    return list(ns)
+
+
+def corr_batch_capture(b, samples, n, vis, fp64=False):
+    return _bcheck(_lib.corr_batch_capture(b, _ptrs(samples), (_i64 * len(n))(*n), _ptrs(vis),
+                                           1 if fp64 else 0), b)
+
+
+def corr_batch_replay(b, n_modes):
+    ns = (_i64 * n_modes)()
+    _bcheck(_lib.corr_batch_replay(b, ns), b)
+    return list(ns)
+
+
+def corr_batch_sync(b):
+    return _bcheck(_lib.corr_batch_sync(b), b)
+
+
+def corr_batch_handle(b, mode):
+    h = _vp()
+    _bcheck(_lib.corr_batch_handle(b, int(mode), ctypes.byref(h)), b)
+    return h
+
+
+def corr_batch_get_stream(b):
+    s = _vp()
+    _bcheck(_lib.corr_batch_get_stream(b, ctypes.byref(s)), b)
+    return s.value or 0
+
+
+def corr_batch_destroy(b):
+    _lib.corr_batch_destroy(b)
+
+
+def corr_batch_last_error(b):
+    m = _lib.corr_batch_last_error(b)
+    return m.decode() if m else ""
+
+
 # ----------------------------------------------------------------------------
 # Convenience object
 # ----------------------------------------------------------------------------
@@ -232,6 +318,66 @@ class Correlator:
         if self.h is not None:
             corr_destroy(self.h)
             self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class CorrelatorBatch:
+    """Several correlators of uneven N and K whose X-engine work shares one
+    persistent tensor-core launch per pass (optionally replayed as a CUDA
+    graph)."""
+
+    def __init__(self, modes, dtype=CORR_FP32, chunk=None, window=0, stages=0):
+        self.modes = [tuple(m) for m in modes]
+        self.b = corr_batch_create([m[0] for m in self.modes], [m[1] for m in self.modes], dtype)
+        self.handles = [corr_batch_handle(self.b, i) for i in range(len(self.modes))]
+        self.info = [corr_info(h) for h in self.handles]
+        if chunk is not None:
+            corr_batch_set_chunk(self.b, chunk)
+        if window or stages:
+            corr_batch_set_tiles(self.b, window, stages)
+
+    @property
+    def stream(self):
+        return corr_batch_get_stream(self.b)
+
+    def push(self, samples, n=None):
+        if n is None:
+            n = [x.numel() * 2 // m[0] for x, m in zip(samples, self.modes)]
+        corr_batch_push(self.b, samples, n)
+
+    def dump(self, vis=None, fp64=False):
+        if vis is None:
+            dt = np.complex128 if fp64 else np.complex64
+            vis = [np.empty((i["P"], i["C"]), dt) for i in self.info]
+        n = corr_batch_dump(self.b, vis, fp64)
+        return vis, n
+
+    def capture(self, samples, vis, n=None, fp64=False):
+        if n is None:
+            n = [x.numel() * 2 // m[0] for x, m in zip(samples, self.modes)]
+        corr_batch_capture(self.b, samples, n, vis, fp64)
+
+    def replay(self):
+        return corr_batch_replay(self.b, len(self.modes))
+
+    def sync(self):
+        corr_batch_sync(self.b)
+
+    def close(self):
+        if self.b is not None:
+            corr_batch_destroy(self.b)
+            self.b = None
 
     def __enter__(self):
         return self

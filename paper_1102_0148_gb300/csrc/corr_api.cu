@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 using namespace gbcorr;
@@ -212,8 +213,11 @@ int estimate_scales(corr_t h, const uint8_t* din, int64_t S) {
 
 // One workspace pass: S frames at `din` (device) -> `acc`.  raw = true skips
 // the per-antenna corrections (the uncorrected visibilities for corr_grad).
-int run_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, double2* acc) {
-    const int64_t S_pad = (S + kSpecPad - 1) / kSpecPad * kSpecPad;
+int64_t pad_frames(int64_t S) { return (S + kSpecPad - 1) / kSpecPad * kSpecPad; }
+
+// F-engine half of a pass: S frames at `din` -> the workspace.
+int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw) {
+    const int64_t S_pad = pad_frames(S);
     if (narrow(h) && !h->scales_ready) {
         int rc = estimate_scales(h, din, S);
         if (rc != CORR_OK) return rc;
@@ -235,7 +239,21 @@ int run_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, double2* acc) {
     prof_begin(h);
     CUDA_TRY(h, launch_fengine(fa, h->stream));
     prof_end(h, CORR_KERNEL_FENGINE);
+    return CORR_OK;
+}
 
+// FP64 reduction of a tensor-core launch's partials, when it wrote any.
+int finish_tc_run(corr_t h, const TcRun& run, double2* acc) {
+    if (run.direct) return CORR_OK;
+    prof_begin(h);
+    CUDA_TRY(h, launch_reduce_partials(h->partial, run.n_split, (int64_t)h->C * h->P, acc,
+                                       h->stream));
+    prof_end(h, CORR_KERNEL_REDUCE);
+    return CORR_OK;
+}
+
+// X-engine half of a pass over the S_pad frames in the workspace -> `acc`.
+int xengine_pass(corr_t h, int64_t S_pad, double2* acc) {
     if (h->use_tc) {
         prof_begin(h);
         TcRun run{};
@@ -248,12 +266,7 @@ int run_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, double2* acc) {
         int rc = tc_launch(plans, 1, &run, h->stream, h->err);
         if (rc != CORR_OK) return rc;
         prof_end(h, CORR_KERNEL_XENGINE);
-        if (!run.direct) {
-            prof_begin(h);
-            CUDA_TRY(h, launch_reduce_partials(h->partial, run.n_split, (int64_t)h->C * h->P, acc,
-                                               h->stream));
-            prof_end(h, CORR_KERNEL_REDUCE);
-        }
+        return finish_tc_run(h, run, acc);
     } else {
         XengineArgs xa{};
         xa.spec = h->spec;
@@ -276,6 +289,12 @@ int run_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, double2* acc) {
         prof_end(h, CORR_KERNEL_REDUCE);
     }
     return CORR_OK;
+}
+
+int run_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, double2* acc) {
+    int rc = fengine_pass(h, din, S, raw);
+    if (rc != CORR_OK) return rc;
+    return xengine_pass(h, pad_frames(S), acc);
 }
 
 // Run every pass of n samples (host or device memory) into `acc`.
@@ -668,5 +687,266 @@ int corr_debug_spectra(corr_t h, const uint8_t* samples, int64_t n, float* spect
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return CORR_OK;
 }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+
+struct corr_batch_s {
+    int n = 0;
+    corr_t h[kMaxTcModes] = {};
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_frames[kMaxTcModes] = {};
+    std::string err = "no error";
+};
+
+namespace {
+
+int batch_err(corr_batch_t b, int code, const char* msg) {
+    b->err = msg;
+    return code;
+}
+
+int batch_from_handle(corr_batch_t b, int m, int rc) {
+    b->err = std::string("mode ") + std::to_string(m) + ": " + b->h[m]->err;
+    return rc;
+}
+
+void batch_free_graph(corr_batch_t b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+int batch_check(corr_batch_t b, const uint8_t* const* samples, const int64_t* n) {
+    if (!samples || !n) return batch_err(b, CORR_EINVAL, "NULL argument");
+    for (int m = 0; m < b->n; ++m) {
+        if (n[m] < 0 || n[m] % b->h[m]->K)
+            return batch_err(b, CORR_EINVAL, "a sample count is not a non-negative multiple of K");
+        if (n[m] > 0 && !is_device_ptr(samples[m]))
+            return batch_err(b, CORR_EINVAL, "batch pushes take device buffers");
+    }
+    return CORR_OK;
+}
+
+// Queue every pass of every mode: per pass index, the F-engine of each mode
+// that has that pass, then one tensor-core launch over all of them.
+int batch_enqueue(corr_batch_t b, const uint8_t* const* samples, const int64_t* n) {
+    int64_t frames[kMaxTcModes], passes = 0;
+    for (int m = 0; m < b->n; ++m) {
+        frames[m] = n[m] / b->h[m]->K;
+        passes = std::max(passes, (frames[m] + b->h[m]->cap - 1) / b->h[m]->cap);
+    }
+    for (int64_t pi = 0; pi < passes; ++pi) {
+        TcPlan* plans[kMaxTcModes];
+        TcRun runs[kMaxTcModes];
+        int idx[kMaxTcModes];
+        int na = 0;
+        for (int m = 0; m < b->n; ++m) {
+            corr_t h = b->h[m];
+            const int64_t f0 = pi * h->cap;
+            if (f0 >= frames[m]) continue;
+            const int64_t S = std::min(h->cap, frames[m] - f0);
+            const int64_t rec = (int64_t)h->N * (h->K / 2);
+            int rc = fengine_pass(h, samples[m] + f0 * rec, S, false);
+            if (rc != CORR_OK) return batch_from_handle(b, m, rc);
+            TcRun r{};
+            r.S_pad = pad_frames(S);
+            r.partial = h->partial;
+            r.acc = h->acc;
+            r.scale = h->scale;
+            r.status = h->status;
+            plans[na] = h->tc;
+            runs[na] = r;
+            idx[na++] = m;
+        }
+        corr_t h0 = b->h[idx[0]];
+        prof_begin(h0);
+        int rc = tc_launch(plans, na, runs, b->stream, b->err);
+        if (rc != CORR_OK) return rc;
+        prof_end(h0, CORR_KERNEL_XENGINE);
+        for (int a = 0; a < na; ++a) {
+            rc = finish_tc_run(b->h[idx[a]], runs[a], b->h[idx[a]]->acc);
+            if (rc != CORR_OK) return batch_from_handle(b, idx[a], rc);
+        }
+    }
+    for (int m = 0; m < b->n; ++m) b->h[m]->n_spec += frames[m];
+    return CORR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int corr_batch_create(corr_batch_t* out, int n_modes, const int* N, const int* K, int dtype) {
+    if (!out) return set_err(nullptr, CORR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_modes < 1 || n_modes > kMaxTcModes || !N || !K)
+        return set_err(nullptr, CORR_EINVAL, "a batch holds 1 to %d modes", kMaxTcModes);
+    if (dtype != CORR_FP32 && dtype != CORR_FP16 && dtype != CORR_FP8E4M3)
+        return set_err(nullptr, CORR_EINVAL, "a batch runs on the tensor cores (FP32, FP16, FP8)");
+    corr_batch_t b = new (std::nothrow) corr_batch_s();
+    if (!b) return set_err(nullptr, CORR_ENOMEM, "host allocation failed");
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return set_err(nullptr, CORR_ECUDA, "stream creation failed");
+    }
+    for (int m = 0; m < n_modes; ++m) {
+        int rc = corr_create(&b->h[m], N[m], K[m], dtype);
+        if (rc == CORR_OK) rc = corr_set_stream(b->h[m], b->stream);
+        if (rc != CORR_OK) {
+            std::string msg = std::string("mode ") + std::to_string(m) + ": " +
+                              corr_last_error(b->h[m] ? b->h[m] : nullptr);
+            b->n = m + 1;
+            corr_batch_destroy(b);
+            return set_err(nullptr, rc, "%s", msg.c_str());
+        }
+        b->n = m + 1;
+    }
+    *out = b;
+    return CORR_OK;
+}
+
+int corr_batch_set_chunk(corr_batch_t b, int64_t max_spectra) {
+    if (!b) return CORR_EINVAL;
+    batch_free_graph(b);
+    for (int m = 0; m < b->n; ++m) {
+        int rc = corr_set_chunk(b->h[m], max_spectra);
+        if (rc != CORR_OK) return batch_from_handle(b, m, rc);
+    }
+    return CORR_OK;
+}
+
+int corr_batch_set_tiles(corr_batch_t b, int window, int stages) {
+    if (!b) return CORR_EINVAL;
+    batch_free_graph(b);
+    for (int m = 0; m < b->n; ++m) {
+        int rc = corr_set_tiles(b->h[m], window, stages);
+        if (rc != CORR_OK) return batch_from_handle(b, m, rc);
+    }
+    return CORR_OK;
+}
+
+int corr_batch_handle(corr_batch_t b, int mode, corr_t* out) {
+    if (!b || !out || mode < 0 || mode >= b->n) return CORR_EINVAL;
+    *out = b->h[mode];
+    return CORR_OK;
+}
+
+int corr_batch_get_stream(corr_batch_t b, void** stream) {
+    if (!b || !stream) return CORR_EINVAL;
+    *stream = b->stream;
+    return CORR_OK;
+}
+
+int corr_batch_push(corr_batch_t b, const uint8_t* const* samples, const int64_t* n) {
+    if (!b) return CORR_EINVAL;
+    int rc = batch_check(b, samples, n);
+    if (rc != CORR_OK) return rc;
+    return batch_enqueue(b, samples, n);
+}
+
+int corr_batch_dump(corr_batch_t b, void* const* vis, int64_t* n_spec, int vis_fp64) {
+    if (!b || !vis) return CORR_EINVAL;
+    for (int m = 0; m < b->n; ++m) {
+        int rc = corr_dump(b->h[m], vis[m], n_spec ? &n_spec[m] : nullptr, vis_fp64);
+        if (rc != CORR_OK) return batch_from_handle(b, m, rc);
+    }
+    return CORR_OK;
+}
+
+int corr_batch_capture(corr_batch_t b, const uint8_t* const* samples, const int64_t* n,
+                       void* const* vis, int vis_fp64) {
+    if (!b || !vis) return CORR_EINVAL;
+    int rc = batch_check(b, samples, n);
+    if (rc != CORR_OK) return rc;
+    for (int m = 0; m < b->n; ++m)
+        if (!is_device_ptr(vis[m])) return batch_err(b, CORR_EINVAL, "captured dumps take device buffers");
+    batch_free_graph(b);
+    // One eager step first: scales, kernel attributes and buffers are settled
+    // outside the capture.
+    rc = batch_enqueue(b, samples, n);
+    if (rc == CORR_OK) rc = corr_batch_dump(b, vis, nullptr, vis_fp64);
+    if (rc != CORR_OK) return rc;
+    bool prof[kMaxTcModes];
+    for (int m = 0; m < b->n; ++m) {
+        prof[m] = b->h[m]->prof_on;
+        b->h[m]->prof_on = false;
+    }
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        rc = batch_enqueue(b, samples, n);
+        for (int m = 0; rc == CORR_OK && m < b->n; ++m) {
+            corr_t h = b->h[m];
+            if (narrow(h) && !h->scales_user)
+                e = launch_scales_from_autos(h->acc, h->N, h->C, h->P, h->n_spec, h->scale_target,
+                                             h->scale, b->stream);
+            if (e == cudaSuccess) e = launch_dump(h->acc, h->C, h->P, vis[m], vis_fp64, b->stream);
+            if (e != cudaSuccess) rc = CORR_ECUDA;
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        if (e2 != cudaSuccess && rc == CORR_OK) {
+            rc = CORR_ECUDA;
+            e = e2;
+        }
+        b->graph = g;
+        if (rc == CORR_OK) {
+            e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+            if (e != cudaSuccess) rc = CORR_ECUDA;
+        }
+    } else {
+        rc = CORR_ECUDA;
+    }
+    for (int m = 0; m < b->n; ++m) {
+        b->h[m]->prof_on = prof[m];
+        b->graph_frames[m] = n[m] / b->h[m]->K;
+        b->h[m]->n_spec = 0;
+    }
+    if (rc != CORR_OK) {
+        cudaGetLastError();
+        batch_free_graph(b);
+        if (rc == CORR_ECUDA)
+            return batch_err(b, rc, (std::string("graph capture: ") + cudaGetErrorString(e)).c_str());
+        return rc;
+    }
+    return CORR_OK;
+}
+
+int corr_batch_replay(corr_batch_t b, int64_t* n_spec) {
+    if (!b) return CORR_EINVAL;
+    if (!b->exec) return batch_err(b, CORR_ESTATE, "no captured step: call corr_batch_capture");
+    cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess)
+        return batch_err(b, CORR_ECUDA, (std::string("graph launch: ") + cudaGetErrorString(e)).c_str());
+    for (int m = 0; n_spec && m < b->n; ++m) n_spec[m] = b->graph_frames[m];
+    return CORR_OK;
+}
+
+int corr_batch_sync(corr_batch_t b) {
+    if (!b) return CORR_EINVAL;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return batch_err(b, CORR_ECUDA, cudaGetErrorString(cudaGetLastError()));
+    for (int m = 0; m < b->n; ++m) {
+        int rc = check_status(b->h[m]);
+        if (rc != CORR_OK) return batch_from_handle(b, m, rc);
+    }
+    return CORR_OK;
+}
+
+void corr_batch_destroy(corr_batch_t b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_free_graph(b);
+    for (int m = 0; m < b->n; ++m) corr_destroy(b->h[m]);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+const char* corr_batch_last_error(corr_batch_t b) { return b ? b->err.c_str() : corr_last_error(nullptr); }
 
 }  // extern "C"

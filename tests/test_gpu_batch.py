@@ -1,0 +1,104 @@
+"""Batching form (GPU): several modes of uneven N and K whose X-engine work
+shares one persistent tensor-core launch per pass, eagerly and replayed as a
+captured CUDA graph.  Every mode's visibilities are checked against the FP64
+oracle with the parity bound of its precision.
+
+The modes are the batching workload's: (44, 512), (22, 2048), (11, 4096) and
+the 256-antenna, K = 1024 scale-up, here at short lengths so the oracle
+finishes in seconds.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1102_0148_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+MODES3 = [(44, 512), (22, 2048), (11, 4096)]
+MODES4 = MODES3 + [(256, 1024)]
+
+
+def norm_err(V, R, N):
+    autos = np.array([oracle.baseline_index(i, i, N) for i in range(N)])
+    A = np.abs(R[autos])
+    pairs = oracle.baseline_pairs(N)
+    nrm = np.sqrt(A[[p[0] for p in pairs]] * A[[p[1] for p in pairs]])
+    return float(np.max(np.abs(np.asarray(V, np.complex128) - R) / np.maximum(nrm, 1e-300)))
+
+
+def make_inputs(modes, T, seed):
+    import torch
+    packed, refs = [], []
+    for m, (N, K) in enumerate(modes):
+        p, _ = synth.make_samples(N, T, K, seed=seed + 100 * m)
+        packed.append(torch.from_numpy(p.reshape(-1)).cuda())
+        refs.append(oracle.correlate(p, N, K)[0])
+    return packed, refs
+
+
+@pytest.mark.parametrize("modes,T", [(MODES3, 1 << 17), (MODES4, 1 << 16)])
+def test_batch_matches_oracle(lib, modes, T):
+    dev, refs = make_inputs(modes, T, seed=11020148 + 40)
+    with lib.CorrelatorBatch(modes, "fp32") as b:
+        b.push(dev)
+        vis, n = b.dump(fp64=True)
+    for (N, K), V, R, nm in zip(modes, vis, refs, n):
+        assert nm == T // K
+        assert norm_err(V, R, N) <= 1e-5, (N, K)
+
+
+def test_batch_multiple_passes(lib):
+    """Chunks smaller than the pushes: the modes have different numbers of
+    passes, so later launches cover only some of them."""
+    modes = MODES3
+    T = 1 << 17                                   # 256, 64 and 32 frames
+    dev, refs = make_inputs(modes, T, seed=11020148 + 41)
+    with lib.CorrelatorBatch(modes, "fp32", chunk=128) as b:
+        b.push(dev)
+        b.push(dev)                               # accumulate twice
+        vis, n = b.dump(fp64=True)
+    for (N, K), V, R, nm in zip(modes, vis, refs, n):
+        assert nm == 2 * T // K
+        assert norm_err(V, 2 * R, N) <= 1e-5
+
+
+def test_batch_graph_replay(lib):
+    import torch
+    modes = MODES3
+    T = 1 << 16
+    dev_a, refs_a = make_inputs(modes, T, seed=11020148 + 42)
+    dev_b, refs_b = make_inputs(modes, T, seed=11020148 + 43)
+    bufs = [x.clone() for x in dev_a]
+    with lib.CorrelatorBatch(modes, "fp32") as b:
+        vis = [torch.empty((N * (N + 1) // 2, K // 2), dtype=torch.complex128, device="cuda")
+               for N, K in modes]
+        b.capture(bufs, vis, fp64=True)
+        for dev, refs in ((dev_a, refs_a), (dev_b, refs_b), (dev_a, refs_a)):
+            for buf, x in zip(bufs, dev):
+                buf.copy_(x)
+            torch.cuda.synchronize()
+            n = b.replay()
+            b.sync()
+            for (N, K), V, R, nm in zip(modes, vis, refs, n):
+                assert nm == T // K
+                assert norm_err(V.cpu().numpy(), R, N) <= 1e-5
+
+
+def test_batch_fp16(lib):
+    modes = MODES3
+    T = 1 << 17
+    dev, refs = make_inputs(modes, T, seed=11020148 + 44)
+    with lib.CorrelatorBatch(modes, "fp16") as b:
+        b.push(dev)
+        vis, n = b.dump(fp64=True)
+    for (N, K), V, R in zip(modes, vis, refs):
+        assert norm_err(V, R, N) <= 1e-3
+
+
+def test_batch_rejects_mixed_or_bad_arguments(lib):
+    with pytest.raises(lib.CorrError):
+        lib.CorrelatorBatch([(44, 512)] * 5, "fp32")
+    with pytest.raises(lib.CorrError):
+        lib.CorrelatorBatch(MODES3, "fp32_simt")

@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the precision / batching / differentiation measurements")
     ap.add_argument("--chunk", type=int, default=0,
                     help="spectra per internal pass (corr_set_chunk); 0 = library default")
     return ap.parse_args()
@@ -382,6 +384,14 @@ def main():
         variants = measure_variants(corr, torch, np, dev_in, pushes, rec, args.dtype, args.chunk)
 
     corr.corr_destroy(h)
+    del dev_in
+    torch.cuda.empty_cache()
+
+    forms = None
+    if rank == 0 and not args.no_forms:
+        forms = {"precision": measure_precision_form(corr, torch, np),
+                 "batching": measure_batch_form(corr, torch, np),
+                 "differentiation": measure_grad_form(corr, torch, np)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -402,7 +412,7 @@ def main():
                        "l2": "inputs (770 MB/step) larger than L2; no flush",
                        "parallelism": f"replicas x{world}"},
             "clocks": clocks, "gpu_launches": launches, "roofline": roofline,
-            "e2e": e2e, "cpu_baseline": cpu, "variants": variants,
+            "e2e": e2e, "cpu_baseline": cpu, "variants": variants, "forms": forms,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -461,6 +471,145 @@ def measure_variants(corr, torch, np, dev_in, pushes, rec, main_dtype, chunk, st
         for name, V in res.items():
             out[name]["err_vs_fp32"] = float(np.max(np.abs(V - ref) / nrm))
     return out
+
+
+def _norm_err(np, V, R, N):
+    autos = [i * N - i * (i - 1) // 2 for i in range(N)]
+    A = np.abs(R[autos])
+    ii = [i for i in range(N) for j in range(i, N)]
+    jj = [j for i in range(N) for j in range(i, N)]
+    nrm = np.sqrt(A[ii] * A[jj])
+    return float(np.max(np.abs(np.asarray(V, np.complex128) - R) / np.maximum(nrm, 1e-300)))
+
+
+def _events_ms(torch, fn, steps, stream):
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def measure_precision_form(corr, torch, np, steps=3):
+    """Full 40 MHz band: N = 44 at 80 MS/s, K = 512, 1 s integrations
+    (156250 spectra) pushed in 2^20-sample chunks; error of each X-engine
+    precision against the FP64 oracle on the 2^20-sample prefix."""
+    import oracle
+    from paper_1102_0148_gb300 import synth
+    rate = 80e6
+    frames = int(rate // K_FFT)
+    rec = N_ANT * K_FFT // 2
+    dev, _ = synth.make_samples_torch(N_ANT, frames * K_FFT, K_FFT, seed=SEED + 1, device="cuda",
+                                      tone_amp=0.5)
+    dev = dev.reshape(-1)
+    R, _ = oracle.correlate(dev[: CHUNK_FRAMES * rec].cpu().numpy(), N_ANT, K_FFT)
+    stream = torch.cuda.current_stream()
+    pushes = [(f0, min(CHUNK_FRAMES, frames - f0)) for f0 in range(0, frames, CHUNK_FRAMES)]
+    out = {"workload": "N=44, K=512, 80 MS/s, 1 s = 156250 spectra; error on the 2^20-sample prefix"}
+    for name in ("fp32", "fp16", "fp8"):
+        with corr.Correlator(N_ANT, K_FFT, name, stream=stream.cuda_stream) as c:
+            c.push(dev[: CHUNK_FRAMES * rec], CHUNK_FRAMES * K_FFT)
+            V, _ = c.dump(fp64=True)
+            err = _norm_err(np, V, R, N_ANT)
+            vis = torch.empty((990, 256), dtype=torch.complex64, device="cuda")
+
+            def step():
+                for f0, nf in pushes:
+                    corr.corr_push(c.h, dev.data_ptr() + f0 * rec, nf * K_FFT)
+                corr.corr_dump(c.h, vis)
+
+            ms = _events_ms(torch, step, steps, stream)
+        val = N_ANT * frames * K_FFT / (ms * 1e-3)
+        out[name] = {"value": val, "unit": UNIT, "rtf": val / (N_ANT * rate), "err_vs_oracle": err}
+    del dev
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_batch_form(corr, torch, np, steps=5):
+    """Modes (44, 512), (22, 2048), (11, 4096) and the (256, 1024) scale-up,
+    2^22 samples per antenna each, in one graph-captured step whose X-engine
+    work is one persistent launch; tiles from a short autotuner sweep.  Error
+    against the FP64 oracle on a 2^16-sample prefix of every mode."""
+    import oracle
+    from paper_1102_0148_gb300 import synth, tune
+    modes = [(44, 512), (22, 2048), (11, 4096), (256, 1024)]
+    T = 1 << 22
+    data = []
+    for m, (N, K) in enumerate(modes):
+        d, _ = synth.make_samples_torch(N, T, K, seed=SEED + 10 + m, device="cuda")
+        data.append(d.reshape(-1))
+    Tp = 1 << 16
+    refs = [oracle.correlate(x[: Tp * N // 2].cpu().numpy(), N, K)[0] for x, (N, K) in zip(data, modes)]
+    out = {"workload": "modes (44,512), (22,2048), (11,4096), (256,1024); 2^22 samples/antenna/mode",
+           "samples_per_step": sum(N * T for N, _ in modes)}
+    for name in ("fp16", "fp32"):
+        t = tune.tune_batch(modes, name, T=T, repeats=2, save=False, windows=(128, 256),
+                            stages=(3, 4, 6))
+        with corr.CorrelatorBatch(modes, name, window=t["window"], stages=t["stages"]) as b:
+            for h, (N, K) in zip(b.handles, modes):
+                corr.corr_set_chunk(h, T // K)           # one pass per mode and push
+            b.push([x[: Tp * N // 2] for x, (N, _) in zip(data, modes)],
+                   [Tp] * len(modes))
+            vis_p, _ = b.dump(fp64=True)
+            errs = [_norm_err(np, V, R, N) for V, R, (N, _) in zip(vis_p, refs, modes)]
+            vis = [torch.empty((N * (N + 1) // 2, K // 2), dtype=torch.complex64, device="cuda")
+                   for N, K in modes]
+            b.capture(data, vis)
+            s = torch.cuda.ExternalStream(b.stream)
+            ms = _events_ms(torch, b.replay, steps, s)
+        val = out["samples_per_step"] / (ms * 1e-3)
+        out[name] = {"value": val, "unit": UNIT, "ms_per_step": ms, "tiles": t,
+                     "err_vs_oracle_per_mode": errs, "x_engine_launches_per_step": 1}
+    del data
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_grad_form(corr, torch, np, steps=5):
+    """N = 44, K = 512, 2^20 samples: L = sum |V(g, tau) - M|^2 with gains
+    g ~ CN(1, 0.1^2) and delays tau ~ U(-0.5, 0.5) applied in the F-engine;
+    forward and backward times and the gradient's error against the
+    oracle's closed form."""
+    import oracle
+    from paper_1102_0148_gb300 import synth
+    from paper_1102_0148_gb300.autograd import visibilities
+    T = 1 << 20
+    packed, _ = synth.make_samples(N_ANT, T, K_FFT, seed=SEED + 5)
+    R, _ = oracle.correlate(packed, N_ANT, K_FFT)
+    g, tau = synth.gains_delays(N_ANT, seed=SEED + 5)
+    g = np.asarray(g, np.complex64).astype(np.complex128)
+    tau = np.asarray(tau, np.float32).astype(np.float64)
+    dev = torch.from_numpy(packed.reshape(-1)).cuda()
+    M = torch.from_numpy(R).cuda()
+    stream = torch.cuda.current_stream()
+    with corr.Correlator(N_ANT, K_FFT, "fp32") as c:
+        gt = torch.tensor(g, dtype=torch.complex64, device="cuda", requires_grad=True)
+        tt = torch.tensor(tau, dtype=torch.float32, device="cuda", requires_grad=True)
+
+        def fwd():
+            return (visibilities(gt, tt, dev, c) - M).abs().pow(2).sum()
+
+        f_ms = _events_ms(torch, fwd, steps, stream)
+
+        def fwd_bwd():
+            gt.grad = None
+            tt.grad = None
+            fwd().backward()
+
+        fb_ms = _events_ms(torch, fwd_bwd, steps, stream)
+        gg = gt.grad.cpu().numpy().astype(np.complex128)
+        gtau = tt.grad.cpu().numpy().astype(np.float64)
+    _, og, ot = oracle.loss_and_grad(R, g, tau, K_FFT)
+    return {"workload": "N=44, K=512, 2^20 samples; loss sum |V(g,tau) - V(1,0)|^2",
+            "forward_ms": f_ms, "backward_ms": fb_ms - f_ms,
+            "grad_g_rel_err": float(np.abs(gg - og).max() / np.abs(og).max()),
+            "grad_tau_rel_err": float(np.abs(gtau - ot).max() / np.abs(ot).max())}
 
 
 if __name__ == "__main__":

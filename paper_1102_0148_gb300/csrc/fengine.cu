@@ -372,6 +372,153 @@ __global__ void __launch_bounds__(kF512Threads, 2) fengine_k512(FengineArgs a) {
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// K = 1024 F-engine: one warp per spectrum, 16 complex points per lane.
+//
+// The 512-point complex transform is split as n = t + 32 j (lane t < 32,
+// register j < 16) and k = k1 + 16 k2:
+//   Z[k1 + 16 k2] = sum_t W32^{t k2} [ W512^{t k1} sum_j z[t + 32 j] W16^{j k1} ].
+// Stage 1 is an in-register 16-point DFT over j and the twiddle W512^{t k1};
+// an exchange through shared memory gives lane l = k1 + 16 h the values of
+// its k1 for t = 16 h .. 16 h + 15.  The 32-point transform over t is a
+// radix-2 step across the two half-warps (one xor-16 shuffle per register):
+//   Z[k1 + 16 h + 32 m] = sum_t' W16^{t' m} W32^{t' h} (B_t' + (-1)^h B_{t'+16})
+// followed by an in-register 16-point DFT over t'.  Lane l ends with
+// Z[k1 + 16 h + 32 m], m < 16; the partner Z[512 - k] of the real split is in
+// lane (16 - k1) mod 16 + 16 (1 - h), register 15 - m (lanes 0 and 16 hold
+// their own partners).
+// ---------------------------------------------------------------------------
+
+constexpr int kF1024Frames = 16;     // frames per CTA, two per warp
+constexpr int kF1024Threads = 256;
+constexpr int kX1024Stride = 33;     // exchange row stride (complex)
+constexpr int kStg1024Row = 1026;    // staging row stride (floats), conflict-free reads
+constexpr int kStg1024Floats = kF1024Frames * kStg1024Row;
+
+template <int OUT>
+__global__ void __launch_bounds__(kF1024Threads, 2) fengine_k1024(FengineArgs a) {
+    constexpr bool DEBUG = OUT == kOutDebug;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* stg = reinterpret_cast<float*>(smem_raw);                        // [16][1026]
+    float2* xch = reinterpret_cast<float2*>(stg + (DEBUG ? 0 : kStg1024Floats));  // [8][16][33]
+    float2* tw_stage = xch + 8 * 16 * kX1024Stride;                         // [16 k1][32 t]
+    float2* tw_post = tw_stage + 512;                                       // [512]
+    float2* tw32 = tw_post + 512;                                           // [16] W32^{t'}
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int k1 = lane & 15;
+    const int hh = lane >> 4;
+    const int i = blockIdx.y;
+    const int64_t s0 = (int64_t)blockIdx.x * kF1024Frames;
+    const float post = OUT == SPEC_F16X2 ? kSplitScale : 1.0f;
+    for (int e = tid; e < 512; e += kF1024Threads) {
+        const int kk = e >> 5, t = e & 31;
+        tw_stage[e] = a.twiddle[2 * t * kk];               // W512^{t k1} = W1024^{2 t k1}
+        const float2 w = a.twiddle[e];
+        tw_post[e] = make_float2(0.5f * post * w.y, -0.5f * post * w.x);
+    }
+    if (tid < 16) tw32[tid] = a.twiddle[32 * tid];         // W32^{t'} = W1024^{32 t'}
+    const float chalf = 0.5f * post;
+
+    uint4 raw0 = make_uint4(0u, 0u, 0u, 0u), raw1 = raw0;
+    {
+        const int64_t sa = s0 + warp, sb = sa + 8;
+        if (sa < a.S) raw0 = __ldg(reinterpret_cast<const uint4*>(a.in + (sa * a.N + i) * 512) + lane);
+        if (sb < a.S) raw1 = __ldg(reinterpret_cast<const uint4*>(a.in + (sb * a.N + i) * 512) + lane);
+    }
+    __syncthreads();
+
+    float2* gx = xch + warp * 16 * kX1024Stride;
+    unsigned char* gbytes = reinterpret_cast<unsigned char*>(gx);
+
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {
+        const int f = warp + 8 * r;
+        const int64_t s = s0 + f;
+        *reinterpret_cast<uint4*>(gbytes + 16 * lane) = r == 0 ? raw0 : raw1;
+        __syncwarp();
+        float2 x[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const unsigned b = gbytes[lane + 32 * j];
+            x[j] = make_float2(nib_lo(b), nib_hi(b));
+        }
+        __syncwarp();
+        dft16(x);
+#pragma unroll
+        for (int q = 1; q < 16; ++q) x[q] = cmul(x[q], tw_stage[q * 32 + lane]);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) gx[q * kX1024Stride + lane] = x[q];
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < 16; ++t) x[t] = gx[k1 * kX1024Stride + 16 * hh + t];
+        __syncwarp();
+        // radix 2 across the half-warps: half 0 forms B_t' + B_t'+16, half 1
+        // W32^{t'} (B_t' - B_t'+16)
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            float2 y;
+            y.x = __shfl_xor_sync(0xffffffffu, x[t].x, 16);
+            y.y = __shfl_xor_sync(0xffffffffu, x[t].y, 16);
+            if (hh == 0) {
+                x[t] = cadd(x[t], y);
+            } else {
+                x[t] = csub(y, x[t]);
+                if (t > 0) x[t] = cmul(x[t], tw32[t]);
+            }
+        }
+        dft16(x);
+        // x[q] = Z[k1 + 16 hh + 32 q]; partner Z[512 - k]
+        const int src = ((16 - k1) & 15) + 16 * (1 - hh);
+        float2 z[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            float2 pz;
+            pz.x = __shfl_sync(0xffffffffu, x[15 - q].x, src);
+            pz.y = __shfl_sync(0xffffffffu, x[15 - q].y, src);
+            if (lane == 0) pz = x[(16 - q) & 15];
+            if (lane == 16) pz = x[15 - q];
+            z[q] = pz;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int k = k1 + 16 * hh + 32 * q;
+            const float2 zk = x[q], zc = z[q];
+            const float2 S = make_float2(zk.x + zc.x, zk.y - zc.y);
+            const float2 D = make_float2(zk.x - zc.x, zk.y + zc.y);
+            const float2 wd = cmul(tw_post[k], D);
+            float2 X = make_float2(fmaf(chalf, S.x, wd.x), fmaf(chalf, S.y, wd.y));
+            if (a.corr) X = cmul(__ldg(a.corr + (int64_t)i * 512 + k), X);
+            if (DEBUG) {
+                if (s < a.S) a.debug_out[((int64_t)i * a.S + s) * 512 + k] = X;
+            } else {
+                if (OUT == SPEC_F16 || OUT == SPEC_F8) {
+                    const float sc = __ldg(a.scale + (int64_t)i * 512 + k);
+                    X.x *= sc;
+                    X.y *= sc;
+                }
+                stg[f * kStg1024Row + k] = X.x;
+                stg[f * kStg1024Row + 512 + k] = X.y;
+            }
+        }
+    }
+    if (DEBUG) return;
+    __syncthreads();
+    // 1024 workspace rows (plane, k) x 16 frames: 4 lanes per row, 4 frames each
+    const int m = lane & 3;
+    for (int row = 8 * warp + (lane >> 2); row < 1024; row += 8 * (kF1024Threads / 32)) {
+        const int plane = row >> 9;
+        const int k = row & 511;
+        const float* src = stg + 4 * m * kStg1024Row + row;
+        const int64_t off = ((int64_t)k * 2 * a.N + spec_row(plane, i, a.N)) * a.ld + s0 + 4 * m;
+        store4<OUT>(a.spec, off, a.plane_stride, src[0], src[kStg1024Row], src[2 * kStg1024Row],
+                    src[3 * kStg1024Row]);
+    }
+}
+
 __global__ void correction_table_kernel(const float2* g, const float* tau, int N, int K,
                                         float2* out) {
     const int C = K / 2;
@@ -415,6 +562,27 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
             case SPEC_F16: return go(fengine_k512<SPEC_F16>);
             case SPEC_F8: return go(fengine_k512<SPEC_F8>);
             default: return go(fengine_k512<SPEC_F16X2>);
+        }
+    }
+    if (a.K == 1024 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0) {
+        const int64_t fr = dbg ? a.S : a.S_pad;
+        if (fr <= 0) return cudaSuccess;
+        dim3 grid((unsigned)((fr + kF1024Frames - 1) / kF1024Frames), (unsigned)a.N);
+        const size_t tables = ((size_t)8 * 16 * kX1024Stride + 512 + 512 + 16) * sizeof(float2);
+        const size_t smem = dbg ? tables : tables + (size_t)kStg1024Floats * sizeof(float);
+        auto go = [&](auto kern) -> cudaError_t {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+            kern<<<grid, kF1024Threads, smem, st>>>(a);
+            return cudaGetLastError();
+        };
+        if (dbg) return go(fengine_k1024<kOutDebug>);
+        switch (a.spec_type) {
+            case SPEC_F32: return go(fengine_k1024<SPEC_F32>);
+            case SPEC_F16: return go(fengine_k1024<SPEC_F16>);
+            case SPEC_F8: return go(fengine_k1024<SPEC_F8>);
+            default: return go(fengine_k1024<SPEC_F16X2>);
         }
     }
     int FT = 8192 / C;

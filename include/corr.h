@@ -174,6 +174,26 @@ int corr_grad(corr_t h, const uint8_t* samples, int64_t n, const float* gains,
               const float* delays, const void* grad_vis, int grad_fp64, float* grad_gains,
               float* grad_delays);
 
+/* Checkpoint / resume of a running integration (no counterpart in the
+ * paper).  corr_state_bytes: size of the state; corr_save_state waits for
+ * the handle's work and copies its FP64 accumulators, spectrum count and
+ * (FP16 / FP8) scales into the host buffer `buf`; corr_load_state restores
+ * them into a handle of the same N, K and dtype (CORR_EINVAL otherwise), so
+ * pushing the rest of the integration and dumping gives what one handle
+ * would have given. */
+int corr_state_bytes(corr_t h, size_t* bytes);
+int corr_save_state(corr_t h, void* buf);
+int corr_load_state(corr_t h, const void* buf);
+
+/* Test hook for the failure path (no counterpart in the paper).  kind 1: in
+ * the next tensor-core X-engine launch, the first work item of CTA 0 never
+ * receives its first operand tile, so the MMA thread's bounded wait expires
+ * after wait_limit_s seconds (0.001..10).  The kernel then records a status
+ * word, drains its own copies, frees its tensor memory and returns; the
+ * next corr_dump / corr_sync reports CORR_ETIMEOUT and the handle stays
+ * usable.  No GPU fault, trap or hang is involved. */
+int corr_test_fault(corr_t h, int kind, double wait_limit_s);
+
 /* Kernel classes reported by corr_profile_read. */
 enum corr_kernel {
     CORR_KERNEL_FENGINE = 0, /* unpack + correction + FFT + corner turn    */

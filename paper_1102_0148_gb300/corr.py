@@ -38,6 +38,10 @@ _SIGS = {
     "corr_set_stream": (_int, [_vp, _vp]),
     "corr_set_chunk": (_int, [_vp, _i64]),
     "corr_set_tiles": (_int, [_vp, _int, _int]),
+    "corr_test_fault": (_int, [_vp, _int, ctypes.c_double]),
+    "corr_state_bytes": (_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "corr_save_state": (_int, [_vp, _vp]),
+    "corr_load_state": (_int, [_vp, _vp]),
     "corr_set_corrections": (_int, [_vp, _vp, _vp]),
     "corr_push": (_int, [_vp, _vp, _i64]),
     "corr_dump": (_int, [_vp, _vp, ctypes.POINTER(_i64), _int]),
@@ -126,6 +130,24 @@ def corr_set_chunk(h, max_spectra):
 
 def corr_set_tiles(h, window=0, stages=0):
     return _check(_lib.corr_set_tiles(h, int(window), int(stages)), h)
+
+
+def corr_save_state(h):
+    """The running integration's state as a bytes object."""
+    n = ctypes.c_size_t(0)
+    _check(_lib.corr_state_bytes(h, ctypes.byref(n)), h)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(_lib.corr_save_state(h, buf), h)
+    return buf.raw
+
+
+def corr_load_state(h, state):
+    buf = ctypes.create_string_buffer(state, len(state))
+    return _check(_lib.corr_load_state(h, buf), h)
+
+
+def corr_test_fault(h, kind, wait_limit_s):
+    return _check(_lib.corr_test_fault(h, int(kind), float(wait_limit_s)), h)
 
 
 def corr_set_corrections(h, gains=None, delays=None):

@@ -478,6 +478,70 @@ int corr_set_tiles(corr_t h, int window, int stages) {
     return tc_set_tiles(h->tc, window, stages, h->err);
 }
 
+// Checkpoint layout: header, FP64 accumulator [C][P], pre-cast scales [N][C]
+// (narrow types only).
+struct StateHeader {
+    uint64_t magic;
+    int32_t N, K, dtype, scales_ready;
+    int64_t n_spec;
+};
+constexpr uint64_t kStateMagic = 0x31726f6362677242ull;   // arbitrary tag
+
+size_t state_bytes(corr_t h) {
+    return sizeof(StateHeader) + (size_t)h->C * h->P * sizeof(double2) +
+           (narrow(h) ? (size_t)h->N * h->C * sizeof(float) : 0);
+}
+
+int corr_state_bytes(corr_t h, size_t* bytes) {
+    if (!h || !bytes) return CORR_EINVAL;
+    *bytes = state_bytes(h);
+    return CORR_OK;
+}
+
+int corr_save_state(corr_t h, void* buf) {
+    if (!h || !buf) return CORR_EINVAL;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    int rc = check_status(h);
+    if (rc != CORR_OK) return rc;
+    StateHeader hd{kStateMagic, h->N, h->K, h->dtype, h->scales_ready ? 1 : 0, h->n_spec};
+    unsigned char* p = static_cast<unsigned char*>(buf);
+    memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    const size_t ab = (size_t)h->C * h->P * sizeof(double2);
+    CUDA_TRY(h, cudaMemcpy(p, h->acc, ab, cudaMemcpyDeviceToHost));
+    if (narrow(h)) CUDA_TRY(h, cudaMemcpy(p + ab, h->scale, (size_t)h->N * h->C * sizeof(float),
+                                          cudaMemcpyDeviceToHost));
+    return CORR_OK;
+}
+
+int corr_load_state(corr_t h, const void* buf) {
+    if (!h || !buf) return CORR_EINVAL;
+    StateHeader hd;
+    memcpy(&hd, buf, sizeof hd);
+    if (hd.magic != kStateMagic) return set_err(h, CORR_EINVAL, "not a correlator state");
+    if (hd.N != h->N || hd.K != h->K || hd.dtype != h->dtype)
+        return set_err(h, CORR_EINVAL, "state of N=%d K=%d dtype=%d does not fit this handle",
+                       (int)hd.N, (int)hd.K, (int)hd.dtype);
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    const unsigned char* p = static_cast<const unsigned char*>(buf) + sizeof hd;
+    const size_t ab = (size_t)h->C * h->P * sizeof(double2);
+    CUDA_TRY(h, cudaMemcpy(h->acc, p, ab, cudaMemcpyHostToDevice));
+    if (narrow(h) && hd.scales_ready) {
+        CUDA_TRY(h, cudaMemcpy(h->scale, p + ab, (size_t)h->N * h->C * sizeof(float),
+                               cudaMemcpyHostToDevice));
+        h->scales_ready = true;
+    }
+    h->n_spec = hd.n_spec;
+    return CORR_OK;
+}
+
+int corr_test_fault(corr_t h, int kind, double wait_limit_s) {
+    if (!h) return CORR_EINVAL;
+    if (kind != 1) return set_err(h, CORR_EINVAL, "unknown fault kind %d", kind);
+    if (!h->use_tc) return set_err(h, CORR_EINVAL, "the withheld-copy fault needs a tensor-core handle");
+    return tc_test_withhold(h->tc, wait_limit_s, h->err);
+}
+
 int corr_set_corrections(corr_t h, const float* gains, const float* delays) {
     if (!h) return CORR_EINVAL;
     if (!gains && !delays) {

@@ -80,6 +80,7 @@ struct TcArgs {
     int gs_floats;            // epilogue G buffer (largest 2nb x (2nb + 1) of the modes)
     int* status;
     unsigned long long timeout_ns;
+    int withhold;             // test hook: CTA 0 does not load its first k-tile
 };
 
 struct Item {
@@ -308,6 +309,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                         ok = false;
                         break;
                     }
+                    if (a.withhold && blockIdx.x == 0 && it == 0) continue;   // test hook
                     const uint32_t fb = smem_u32(&full[st]);
                     mbar_expect_tx(fb, bytes);
                     const uint32_t dst = smem_u32(stages + st * stage_bytes);
@@ -579,6 +581,8 @@ struct TcPlan {
     int window = 0;           // 0 = kDefaultWindow
     int stages = 0;           // 0 = as many as shared memory allows
     unsigned long long timeout_ns = 4000000000ull;
+    int withhold = 0;                    // test hook for the next launch
+    unsigned long long hook_timeout_ns = 0;
     // split decisions already made, keyed by the S_pad of every mode in the launch
     std::vector<std::pair<std::vector<int64_t>, std::vector<int>>> split_cache;
 };
@@ -759,6 +763,11 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
     a.gs_floats = L.gs_floats;
     a.status = runs[0].status;
     a.timeout_ns = plans[0]->timeout_ns;
+    if (plans[0]->withhold) {
+        a.withhold = 1;
+        a.timeout_ns = plans[0]->hook_timeout_ns;
+        plans[0]->withhold = 0;
+    }
     int base = 0;
     for (int m = 0; m < n; ++m) {
         const TcPlan* p = plans[m];
@@ -805,6 +814,16 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
         err = std::string("tensor-core X-engine launch: ") + cudaGetErrorString(e);
         return CORR_ECUDA;
     }
+    return CORR_OK;
+}
+
+int tc_test_withhold(TcPlan* p, double wait_limit_s, std::string& err) {
+    if (!(wait_limit_s >= 0.001 && wait_limit_s <= 10.0)) {
+        err = "wait limit must be in [0.001, 10] s";
+        return CORR_EINVAL;
+    }
+    p->withhold = 1;
+    p->hook_timeout_ns = (unsigned long long)(wait_limit_s * 1e9);
     return CORR_OK;
 }
 

@@ -33,6 +33,9 @@ int tc_set_tiles(TcPlan* p, int window, int stages, std::string& err);
 // Modes whose run reports direct = false need the reduction of their
 // n_split partial blocks into acc.
 int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::string& err);
+// Test hook: the next launch's CTA 0 skips the copy of its first k-tile, so
+// its MMA thread's bounded wait expires after wait_limit_s.
+int tc_test_withhold(TcPlan* p, double wait_limit_s, std::string& err);
 void tc_plan_destroy(TcPlan* p);
 
 }  // namespace gbcorr

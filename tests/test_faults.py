@@ -1,0 +1,98 @@
+"""Failure detection without a GPU fault.
+
+* A bounded device-side wait that runs out: the test hook withholds one
+  operand copy of the next tensor-core launch (a signal nothing will send),
+  the wait expires after 50 ms, the kernel records a status and returns,
+  the host reports CORR_ETIMEOUT, and the same handle then correlates
+  correctly.
+* Calls made in the wrong state or with bad arguments fail with their status
+  and leave the integration as it was.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1102_0148_gb300 import synth
+
+
+def _err(V, R, N):
+    autos = [oracle.baseline_index(i, i, N) for i in range(N)]
+    A = np.abs(R[autos])
+    pairs = oracle.baseline_pairs(N)
+    nrm = np.sqrt(A[[p[0] for p in pairs]] * A[[p[1] for p in pairs]])
+    return float(np.max(np.abs(V - R) / nrm))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", ["fp32", "fp16"])
+def test_bounded_wait_timeout_is_reported_and_recovered(lib, dtype):
+    import torch
+    N, K, S = 8, 512, 512
+    packed, _ = synth.make_samples(N, S * K, K, seed=77)
+    R, _ = oracle.correlate(packed, N, K)
+    dev = torch.from_numpy(packed.reshape(-1)).cuda()
+    with lib.Correlator(N, K, dtype) as c:
+        lib.corr_test_fault(c.h, 1, 0.05)
+        c.push(dev, S * K)                       # queued; the X-engine gives up
+        with pytest.raises(lib.CorrError) as ei:
+            c.dump(fp64=True)
+        assert ei.value.code == lib.CORR_ETIMEOUT
+        assert "bounded" in str(ei.value)
+        c.push(dev, S * K)                       # the handle is still usable
+        V, n = c.dump(fp64=True)
+    assert n == S
+    assert _err(V, R, N) <= (1e-5 if dtype == "fp32" else 1e-3)
+
+
+@pytest.mark.gpu
+def test_state_errors_leave_integration_intact(lib):
+    import torch
+    N, K, S = 6, 64, 100
+    packed, _ = synth.make_samples(N, S * K, K, seed=78)
+    R, _ = oracle.correlate(packed, N, K)
+    dev = torch.from_numpy(packed.reshape(-1)).cuda()
+    with lib.Correlator(N, K, "fp32") as c:
+        c.push(dev, S * K)
+        with pytest.raises(lib.CorrError) as ei:
+            lib.corr_set_chunk(c.h, 256)         # not between integrations
+        assert ei.value.code == lib.CORR_ESTATE
+        with pytest.raises(lib.CorrError) as ei:
+            lib.corr_set_tiles(c.h, 100, 0)      # not a multiple of the k-tile
+        assert ei.value.code == lib.CORR_EINVAL
+        with pytest.raises(lib.CorrError) as ei:
+            lib.corr_test_fault(c.h, 9, 0.05)
+        assert ei.value.code == lib.CORR_EINVAL
+        V, n = c.dump(fp64=True)
+    assert n == S and _err(V, R, N) <= 1e-5
+    with lib.Correlator(N, K, "fp16") as c:
+        with pytest.raises(lib.CorrError) as ei:
+            lib.corr_get_scales(c.h)             # nothing pushed yet
+        assert ei.value.code == lib.CORR_ESTATE
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", ["fp32", "fp8"])
+def test_checkpoint_resume_equals_one_run(lib, dtype):
+    import torch
+    N, K = 10, 512
+    packed, _ = synth.make_samples(N, 600 * K, K, seed=79)
+    dev = torch.from_numpy(packed.reshape(-1)).cuda()
+    rec = N * K // 2
+    with lib.Correlator(N, K, dtype) as c:
+        c.push(dev[: 300 * rec], 300 * K)
+        c.push(dev[300 * rec:], 300 * K)
+        V_one, n_one = c.dump(fp64=True)
+    with lib.Correlator(N, K, dtype) as c:
+        c.push(dev[: 300 * rec], 300 * K)
+        state = lib.corr_save_state(c.h)
+    with lib.Correlator(N, K, dtype) as c2:
+        lib.corr_load_state(c2.h, state)
+        c2.push(dev[300 * rec:], 300 * K)
+        V_two, n_two = c2.dump(fp64=True)
+    assert n_one == n_two == 600
+    assert np.array_equal(V_one, V_two)
+    with lib.Correlator(N + 1, K, dtype) as c3:
+        with pytest.raises(lib.CorrError) as ei:
+            lib.corr_load_state(c3.h, state)
+        assert ei.value.code == lib.CORR_EINVAL

@@ -559,8 +559,9 @@ def measure_batch_form(corr, torch, np, steps=5):
            "samples_per_step": sum(N * T for N, _ in modes)}
     for name in ("fp16", "fp32"):
         t = tune.tune_batch(modes, name, T=T, repeats=2, save=False, windows=(128, 256),
-                            stages=(3, 4, 6))
-        with corr.CorrelatorBatch(modes, name, window=t["window"], stages=t["stages"]) as b:
+                            stages=(3, 4, 6), splits=(0, 2))
+        with corr.CorrelatorBatch(modes, name, window=t["window"], stages=t["stages"],
+                                  split=t["split"]) as b:
             for h, (N, K) in zip(b.handles, modes):
                 corr.corr_set_chunk(h, T // K)           # one pass per mode and push
             b.push([x[: Tp * N // 2] for x, (N, _) in zip(data, modes)],

@@ -96,19 +96,26 @@ int corr_create(corr_t* out, int N, int K, int dtype);
  * first. */
 int corr_set_stream(corr_t h, void* stream);
 
-/* Largest number of spectra processed per internal pass (the spectra
- * workspace holds this many frames).  Rounded up to a multiple of 128;
- * default 2048.  Reallocates the workspace; only valid with nothing pushed
- * since the last dump. */
+/* Capacity of the spectra workspace in frames, rounded up to a multiple of
+ * 128; default 8192 (halved while the workspace would exceed 2 GiB, not below
+ * 2048).  Pushes are transformed by the F-engine as they arrive and collected
+ * in the workspace; the X-engine runs when it is full, at a push whose frame
+ * count is not a multiple of 128, and at corr_dump / corr_sync.  Reallocates
+ * the workspace; only valid with nothing pushed since the last dump. */
 int corr_set_chunk(corr_t h, int64_t max_spectra);
 
 /* Tile choices of the tensor-core X-engine (no counterpart in the paper; the
  * autotuner in paper_1102_0148_gb300/tune.py picks them): `window` = spectra
  * accumulated in TMEM before the epilogue adds them up in FP32 (a multiple
- * of 64, of 128 for FP8; 0 = 128), `stages` = depth of the shared-memory
- * operand ring (2..16, clipped to what shared memory holds; 0 = automatic).
- * CORR_EINVAL for CUDA-core handles or out-of-range values. */
-int corr_set_tiles(corr_t h, int window, int stages);
+ * of 64, of 128 for FP8; 0 = 256 in FP32 mode, 512 for FP16 / FP8), `stages` = depth of the shared-memory
+ * operand ring (2..16, clipped to what shared memory holds; 0 = automatic),
+ * `split` = ranges of spectra per channel and antenna-block pair into which
+ * a pass is cut (1..64, partials combined in a fixed order inside the
+ * launch; 0 = chosen by the planner), `atoms` = k-tiles (64 spectra, 128 for
+ * FP8) carried by one pipeline stage (1..4; 0 = as many as leave three
+ * stages).  The window is rounded up to whole stages.  CORR_EINVAL for
+ * CUDA-core handles or out-of-range values. */
+int corr_set_tiles(corr_t h, int window, int stages, int split, int atoms);
 
 /* Per-antenna corrections of Sec. 2.1.  gains: N complex values as 2N floats
  * (re, im); delays: N floats, in samples.  Either may be NULL (gain 1,
@@ -252,7 +259,7 @@ typedef struct corr_batch_s* corr_batch_t;
 
 int corr_batch_create(corr_batch_t* out, int n_modes, const int* N, const int* K, int dtype);
 int corr_batch_set_chunk(corr_batch_t b, int64_t max_spectra);
-int corr_batch_set_tiles(corr_batch_t b, int window, int stages);
+int corr_batch_set_tiles(corr_batch_t b, int window, int stages, int split, int atoms);
 int corr_batch_push(corr_batch_t b, const uint8_t* const* samples, const int64_t* n);
 int corr_batch_dump(corr_batch_t b, void* const* vis, int64_t* n_spec, int vis_fp64);
 int corr_batch_capture(corr_batch_t b, const uint8_t* const* samples, const int64_t* n,

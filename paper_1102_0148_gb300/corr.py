@@ -37,7 +37,7 @@ _SIGS = {
     "corr_create": (_int, [ctypes.POINTER(_vp), _int, _int, _int]),
     "corr_set_stream": (_int, [_vp, _vp]),
     "corr_set_chunk": (_int, [_vp, _i64]),
-    "corr_set_tiles": (_int, [_vp, _int, _int]),
+    "corr_set_tiles": (_int, [_vp, _int, _int, _int, _int]),
     "corr_test_fault": (_int, [_vp, _int, ctypes.c_double]),
     "corr_state_bytes": (_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "corr_save_state": (_int, [_vp, _vp]),
@@ -56,7 +56,7 @@ _SIGS = {
     "corr_set_scales": (_int, [_vp, _vp]),
     "corr_batch_create": (_int, [ctypes.POINTER(_vp), _int, ctypes.POINTER(_int), ctypes.POINTER(_int), _int]),
     "corr_batch_set_chunk": (_int, [_vp, _i64]),
-    "corr_batch_set_tiles": (_int, [_vp, _int, _int]),
+    "corr_batch_set_tiles": (_int, [_vp, _int, _int, _int, _int]),
     "corr_batch_push": (_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i64)]),
     "corr_batch_dump": (_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i64), _int]),
     "corr_batch_capture": (_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.POINTER(_vp), _int]),
@@ -128,8 +128,8 @@ def corr_set_chunk(h, max_spectra):
     return _check(_lib.corr_set_chunk(h, int(max_spectra)), h)
 
 
-def corr_set_tiles(h, window=0, stages=0):
-    return _check(_lib.corr_set_tiles(h, int(window), int(stages)), h)
+def corr_set_tiles(h, window=0, stages=0, split=0, atoms=0):
+    return _check(_lib.corr_set_tiles(h, int(window), int(stages), int(split), int(atoms)), h)
 
 
 def corr_save_state(h):
@@ -253,8 +253,9 @@ def corr_batch_set_chunk(b, max_spectra):
     return _bcheck(_lib.corr_batch_set_chunk(b, int(max_spectra)), b)
 
 
-def corr_batch_set_tiles(b, window=0, stages=0):
-    return _bcheck(_lib.corr_batch_set_tiles(b, int(window), int(stages)), b)
+def corr_batch_set_tiles(b, window=0, stages=0, split=0, atoms=0):
+    return _bcheck(_lib.corr_batch_set_tiles(b, int(window), int(stages), int(split), int(atoms)),
+                   b)
 
 
 def corr_batch_push(b, samples, n):
@@ -359,15 +360,15 @@ class CorrelatorBatch:
     persistent tensor-core launch per pass (optionally replayed as a CUDA
     graph)."""
 
-    def __init__(self, modes, dtype=CORR_FP32, chunk=None, window=0, stages=0):
+    def __init__(self, modes, dtype=CORR_FP32, chunk=None, window=0, stages=0, split=0):
         self.modes = [tuple(m) for m in modes]
         self.b = corr_batch_create([m[0] for m in self.modes], [m[1] for m in self.modes], dtype)
         self.handles = [corr_batch_handle(self.b, i) for i in range(len(self.modes))]
         self.info = [corr_info(h) for h in self.handles]
         if chunk is not None:
             corr_batch_set_chunk(self.b, chunk)
-        if window or stages:
-            corr_batch_set_tiles(self.b, window, stages)
+        if window or stages or split:
+            corr_batch_set_tiles(self.b, window, stages, split)
 
     @property
     def stream(self):

@@ -17,7 +17,11 @@ using namespace gbcorr;
 
 namespace {
 
-constexpr int64_t kDefaultChunk = 2048;
+// Default workspace: 8192 frames (four 2^20-sample pushes at K = 512), fewer
+// when that would exceed 2 GiB, but at least 2048.
+constexpr int64_t kDefaultChunk = 8192;
+constexpr int64_t kMinDefaultChunk = 2048;
+constexpr size_t kDefaultWorkspaceBytes = (size_t)2 << 30;
 constexpr int64_t kSimtSplit = 256;   // frames per SIMT X-engine split
 
 thread_local std::string g_create_error = "no error";
@@ -55,6 +59,8 @@ struct corr_s {
     int stage_next = 0;
     void* vis_dev = nullptr;
     int64_t n_spec = 0;
+    int64_t fill = 0;            // frames waiting in the workspace for the X-engine
+    double2* fill_acc = nullptr; // accumulator those frames belong to
     TcPlan* tc = nullptr;
     // instrumentation: CUDA event pairs per kernel class
     bool prof_on = false;
@@ -147,6 +153,7 @@ int check_status(corr_t h) {
     CUDA_TRY(h, cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st != 0) {
         CUDA_TRY(h, cudaMemset(h->status, 0, sizeof(int)));
+        if (h->tc) tc_reset(h->tc);
         return set_err(h, CORR_ETIMEOUT, "a bounded device-side wait gave up (code %d)", st);
     }
     return CORR_OK;
@@ -216,7 +223,7 @@ int estimate_scales(corr_t h, const uint8_t* din, int64_t S) {
 int64_t pad_frames(int64_t S) { return (S + kSpecPad - 1) / kSpecPad * kSpecPad; }
 
 // F-engine half of a pass: S frames at `din` -> the workspace.
-int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw) {
+int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off = 0) {
     const int64_t S_pad = pad_frames(S);
     if (narrow(h) && !h->scales_ready) {
         int rc = estimate_scales(h, din, S);
@@ -230,7 +237,7 @@ int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw) {
     fa.S_pad = S_pad;
     fa.twiddle = h->twiddle;
     fa.corr = (h->corr_on && !raw) ? h->corr_tab : nullptr;
-    fa.spec = h->spec;
+    fa.spec = static_cast<unsigned char*>(h->spec) + off * spec_elem_bytes(h->spec_type);
     fa.ld = h->cap;
     fa.plane_stride = (int64_t)h->C * 2 * h->N * h->cap;
     fa.spec_type = h->spec_type;
@@ -297,7 +304,38 @@ int run_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, double2* acc) {
     return xengine_pass(h, pad_frames(S), acc);
 }
 
-// Run every pass of n samples (host or device memory) into `acc`.
+// X-engine over the frames waiting in the workspace.
+int flush(corr_t h) {
+    if (h->fill == 0) return CORR_OK;
+    const int64_t f = h->fill;
+    h->fill = 0;
+    return xengine_pass(h, f, h->fill_acc);
+}
+
+// F-engine of S frames into the workspace after the frames already waiting
+// there; the X-engine runs once the workspace is full, or at once when S is
+// not a multiple of the 128-frame padding (the padding must stay at the end).
+int stage_frames(corr_t h, const uint8_t* din, int64_t S, bool raw, double2* acc) {
+    if (h->fill > 0 && acc != h->fill_acc) {
+        int rc = flush(h);
+        if (rc != CORR_OK) return rc;
+    }
+    if (narrow(h) && !h->scales_ready) {
+        int rc = flush(h);                       // the estimate uses the workspace
+        if (rc == CORR_OK) rc = estimate_scales(h, din, S);
+        if (rc != CORR_OK) return rc;
+    }
+    h->fill_acc = acc;
+    int rc = fengine_pass(h, din, S, raw, h->fill);
+    if (rc != CORR_OK) return rc;
+    const bool whole = S % kSpecPad == 0;
+    h->fill += whole ? S : pad_frames(S);
+    if (!whole || h->fill >= h->cap) return flush(h);
+    return CORR_OK;
+}
+
+// Transform n samples (host or device memory) into the workspace, running the
+// X-engine into `acc` whenever it fills up.
 int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, double2* acc) {
     const int64_t frames = n / h->K;
     const int64_t rec = (int64_t)h->N * (h->K / 2);
@@ -309,8 +347,13 @@ int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, doubl
             CUDA_TRY(h, cudaEventCreateWithFlags(&h->stage_full[b], cudaEventDisableTiming));
         }
     }
-    for (int64_t f0 = 0; f0 < frames; f0 += h->cap) {
-        const int64_t S = frames - f0 < h->cap ? frames - f0 : h->cap;
+    for (int64_t f0 = 0; f0 < frames;) {
+        if (h->fill > 0 && acc != h->fill_acc) {
+            int rc = flush(h);
+            if (rc != CORR_OK) return rc;
+        }
+        const int64_t room = h->cap - h->fill;
+        const int64_t S = frames - f0 < room ? frames - f0 : room;
         const uint8_t* din = samples + f0 * rec;
         int b = 0;
         if (host) {
@@ -323,9 +366,10 @@ int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, doubl
             CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->stage_full[b], 0));
             din = h->stage[b];
         }
-        int rc = run_pass(h, din, S, raw, acc);
+        int rc = stage_frames(h, din, S, raw, acc);
         if (rc != CORR_OK) return rc;
         if (host) CUDA_TRY(h, cudaEventRecord(h->stage_free[b], h->stream));
+        f0 += S;
     }
     return CORR_OK;
 }
@@ -442,7 +486,11 @@ int corr_create(corr_t* out, int N, int K, int dtype) {
             cudaSuccess)
             return bail(set_err(h, CORR_ECUDA, "initialisation copy failed"));
     }
-    int rc = alloc_workspace(h, kDefaultChunk);
+    int64_t chunk = kDefaultChunk;
+    const size_t per_frame = (size_t)spec_planes(h->spec_type) * h->C * 2 * h->N *
+                             spec_elem_bytes(h->spec_type);
+    while (chunk > kMinDefaultChunk && (size_t)chunk * per_frame > kDefaultWorkspaceBytes) chunk /= 2;
+    int rc = alloc_workspace(h, chunk);
     if (rc != CORR_OK) return bail(rc);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess)
         return bail(set_err(h, CORR_ECUDA, "initialisation failed"));
@@ -472,10 +520,10 @@ int corr_set_chunk(corr_t h, int64_t max_spectra) {
     return alloc_workspace(h, max_spectra);
 }
 
-int corr_set_tiles(corr_t h, int window, int stages) {
+int corr_set_tiles(corr_t h, int window, int stages, int split, int atoms) {
     if (!h) return CORR_EINVAL;
     if (!h->use_tc) return set_err(h, CORR_EINVAL, "tile choices apply to tensor-core handles");
-    return tc_set_tiles(h->tc, window, stages, h->err);
+    return tc_set_tiles(h->tc, window, stages, split, atoms, h->err);
 }
 
 // Checkpoint layout: header, FP64 accumulator [C][P], pre-cast scales [N][C]
@@ -500,6 +548,8 @@ int corr_state_bytes(corr_t h, size_t* bytes) {
 
 int corr_save_state(corr_t h, void* buf) {
     if (!h || !buf) return CORR_EINVAL;
+    int frc = flush(h);
+    if (frc != CORR_OK) return frc;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     int rc = check_status(h);
     if (rc != CORR_OK) return rc;
@@ -522,6 +572,8 @@ int corr_load_state(corr_t h, const void* buf) {
     if (hd.N != h->N || hd.K != h->K || hd.dtype != h->dtype)
         return set_err(h, CORR_EINVAL, "state of N=%d K=%d dtype=%d does not fit this handle",
                        (int)hd.N, (int)hd.K, (int)hd.dtype);
+    int frc = flush(h);                  // pending frames are replaced with the state
+    if (frc != CORR_OK) return frc;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     const unsigned char* p = static_cast<const unsigned char*>(buf) + sizeof hd;
     const size_t ab = (size_t)h->C * h->P * sizeof(double2);
@@ -606,9 +658,12 @@ int corr_grad(corr_t h, const uint8_t* samples, int64_t n, const float* gains,
         CUDA_TRY(h, cudaMemcpyAsync(gv_dev, grad_vis, gv_bytes, cudaMemcpyHostToDevice, h->stream));
         gv = gv_dev;
     }
+    int frc = flush(h);                  // the running integration's pending frames
+    if (frc != CORR_OK) return frc;
     CUDA_TRY(h, cudaMemsetAsync(h->acc_raw, 0, CPb * sizeof(double2), h->stream));
     if (n > 0) {
         int rc = process_samples(h, samples, n, true, h->acc_raw);
+        if (rc == CORR_OK) rc = flush(h);
         if (rc != CORR_OK) return rc;
     }
     CUDA_TRY(h, launch_grad(h->acc_raw, gv, grad_fp64, gains ? g_dev : nullptr,
@@ -624,6 +679,8 @@ int corr_grad(corr_t h, const uint8_t* samples, int64_t n, const float* gains,
 int corr_dump(corr_t h, void* vis, int64_t* n_spec, int vis_fp64) {
     if (!h) return CORR_EINVAL;
     if (!vis) return set_err(h, CORR_EINVAL, "vis is NULL");
+    int frc = flush(h);
+    if (frc != CORR_OK) return frc;
     const size_t bytes = (size_t)h->C * h->P * (vis_fp64 ? sizeof(double2) : sizeof(float2));
     const bool dev = is_device_ptr(vis);
     void* out = vis;
@@ -650,6 +707,8 @@ int corr_dump(corr_t h, void* vis, int64_t* n_spec, int vis_fp64) {
 
 int corr_sync(corr_t h) {
     if (!h) return CORR_EINVAL;
+    int frc = flush(h);
+    if (frc != CORR_OK) return frc;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return check_status(h);
 }
@@ -671,6 +730,8 @@ int corr_info(corr_t h, int* N, int* K, int* C, int* P, int* dtype) {
 int corr_set_scales(corr_t h, const float* scales) {
     if (!h) return CORR_EINVAL;
     if (!narrow(h)) return set_err(h, CORR_EINVAL, "scales apply to CORR_FP16 / CORR_FP8E4M3 handles");
+    int frc = flush(h);                  // waiting frames were cast with the old scales
+    if (frc != CORR_OK) return frc;
     if (!scales) {
         h->scales_user = false;
         h->scales_ready = false;
@@ -885,11 +946,11 @@ int corr_batch_set_chunk(corr_batch_t b, int64_t max_spectra) {
     return CORR_OK;
 }
 
-int corr_batch_set_tiles(corr_batch_t b, int window, int stages) {
+int corr_batch_set_tiles(corr_batch_t b, int window, int stages, int split, int atoms) {
     if (!b) return CORR_EINVAL;
     batch_free_graph(b);
     for (int m = 0; m < b->n; ++m) {
-        int rc = corr_set_tiles(b->h[m], window, stages);
+        int rc = corr_set_tiles(b->h[m], window, stages, split, atoms);
         if (rc != CORR_OK) return batch_from_handle(b, m, rc);
     }
     return CORR_OK;

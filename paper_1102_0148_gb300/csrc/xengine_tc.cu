@@ -58,7 +58,7 @@ constexpr int kRowBytes = 128;      // one swizzle span per row
 constexpr int kTileBytes = kRows * kRowBytes;
 constexpr uint32_t kTmemCols = 512; // two accumulator sets of 256 columns
 constexpr int kStatusTimeout = 2;
-constexpr int kDefaultWindow = 128; // spectra per TMEM accumulation window
+constexpr int kVB = 2;              // accumulator loads in flight per epilogue thread
 
 struct TcModeArgs {
     int N, C, P;
@@ -66,8 +66,9 @@ struct TcModeArgs {
     int n_split;
     int item_base, n_items;   // items: channel fastest, then block pair, then split
     int64_t S_pad, S_item;
-    float2* partial;          // [n_split][C][P] FP32 partials (acc == nullptr)
-    double2* acc;             // [C][P] FP64 accumulator, added to directly
+    float2* partial;          // [n_split][C][P] FP32 partials (n_split > 1)
+    double2* acc;             // [C][P] FP64 accumulator
+    int* ticket;              // [C][npairs] arrival counters (n_split > 1), zero between launches
     const float* scale;       // [N][C] pre-cast scales (modes 1, 2)
 };
 
@@ -76,6 +77,7 @@ struct TcArgs {
     TcModeArgs md[kMaxTcModes];
     int n_modes, total_items;
     int stages, KT, W;
+    int atoms;                // k-tiles of KT spectra per pipeline stage
     int two_tiles;            // stage slots hold separate A and B tiles
     int gs_floats;            // epilogue G buffer (largest 2nb x (2nb + 1) of the modes)
     int* status;
@@ -84,7 +86,7 @@ struct TcArgs {
 };
 
 struct Item {
-    int m, k, b1, b2, sp;
+    int m, k, b1, b2, sp, pr;
 };
 
 __device__ __forceinline__ Item decode_item(const TcArgs& a, int g) {
@@ -97,6 +99,7 @@ __device__ __forceinline__ Item decode_item(const TcArgs& a, int g) {
     it.k = l % d.C;
     l /= d.C;
     int pr = l % d.npairs;
+    it.pr = pr;
     it.sp = l / d.npairs;
     int b1 = 0;
     while (pr >= d.nblk - b1) {
@@ -241,8 +244,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     constexpr int planes = MODE == 0 ? 2 : 1;
-    constexpr uint32_t tile_set = planes * kTileBytes;          // one operand, all planes
+    // stage layout: [operand A|B][plane][atom] tiles of 16 KB
+    const uint32_t tile_set = planes * a.atoms * kTileBytes;    // one operand, all planes
     const uint32_t stage_bytes = tile_set * (a.two_tiles ? 2u : 1u);
+    const uint32_t plane_off = (uint32_t)a.atoms * kTileBytes;   // hi -> lo plane
+    const int step = a.KT * a.atoms;                             // spectra per stage
     unsigned char* stages = smem;
     float* Gs = reinterpret_cast<float*>(smem + a.stages * stage_bytes);   // <= 128 x 129
     uint64_t* bars = reinterpret_cast<uint64_t*>(
@@ -254,7 +260,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
     uint64_t* drain = acce + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_word = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    volatile int* epi_ok = abort_word + 1;
+    volatile int* epi_last = abort_word + 2;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -266,7 +272,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&accf[b]), 1);
-            mbar_init(smem_u32(&acce[b]), 256);
+            mbar_init(smem_u32(&acce[b]), 8);      // one arrival per epilogue warp
         }
         mbar_init(smem_u32(drain), 1);
         *abort_word = 0;
@@ -297,12 +303,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                 const TcModeArgs& d = a.md[itm.m];
                 const CUtensorMap* map = &a.tmap[itm.m];
                 const bool diag = itm.b1 == itm.b2;
-                const uint32_t bytes = tile_set * (diag ? 1u : 2u);
                 const int ra = kRows * itm.b1;
                 const int rb = kRows * itm.b2;
                 const int64_t s_beg = (int64_t)itm.sp * d.S_item;
                 const int64_t s_end = min(d.S_pad, s_beg + d.S_item);
-                for (int64_t s = s_beg; s < s_end; s += a.KT, ++it) {
+                for (int64_t s = s_beg; s < s_end; s += step, ++it) {
                     const uint32_t st = it % a.stages;
                     const uint32_t ph = (it / a.stages) & 1u;
                     if (!wait_bar(smem_u32(&empty[st]), ph ^ 1u, abort_word, a)) {
@@ -310,15 +315,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                         break;
                     }
                     if (a.withhold && blockIdx.x == 0 && it == 0) continue;   // test hook
+                    const int n_at = (int)min((int64_t)a.atoms, (s_end - s) / a.KT);
+                    const uint32_t bytes =
+                        (uint32_t)n_at * planes * kTileBytes * (diag ? 1u : 2u);
                     const uint32_t fb = smem_u32(&full[st]);
                     mbar_expect_tx(fb, bytes);
                     const uint32_t dst = smem_u32(stages + st * stage_bytes);
-                    tma_load_3d(dst, map, fb, (int)s, ra, itm.k);
-                    if (planes == 2) tma_load_3d(dst + kTileBytes, map, fb, (int)s, ra, d.C + itm.k);
-                    if (!diag) {
-                        tma_load_3d(dst + tile_set, map, fb, (int)s, rb, itm.k);
-                        if (planes == 2)
-                            tma_load_3d(dst + tile_set + kTileBytes, map, fb, (int)s, rb, d.C + itm.k);
+                    for (int at = 0; at < n_at; ++at) {
+                        const int sa = (int)s + at * a.KT;
+                        const uint32_t o = (uint32_t)at * kTileBytes;
+                        tma_load_3d(dst + o, map, fb, sa, ra, itm.k);
+                        if (planes == 2) tma_load_3d(dst + plane_off + o, map, fb, sa, ra, d.C + itm.k);
+                        if (!diag) {
+                            tma_load_3d(dst + tile_set + o, map, fb, sa, rb, itm.k);
+                            if (planes == 2)
+                                tma_load_3d(dst + tile_set + plane_off + o, map, fb, sa, rb, d.C + itm.k);
+                        }
                     }
                     armed_phase[st] = (int)ph;
                 }
@@ -363,7 +375,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                     const uint32_t d1 = d0 + 128u;
                     const int64_t w1 = min(s_end, w0 + a.W);
                     uint32_t acc = 0;
-                    for (int64_t s = w0; s < w1; s += a.KT, ++it) {
+                    for (int64_t s = w0; s < w1; s += step, ++it) {
                         const uint32_t st = it % a.stages;
                         const uint32_t ph = (it / a.stages) & 1u;
                         if (!wait_bar(smem_u32(&full[st]), ph, abort_word, a)) {
@@ -372,26 +384,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                         }
                         tc_fence_after();
                         const uint32_t base = smem_u32(stages + st * stage_bytes);
+                        const int n_at = (int)min((int64_t)a.atoms, (w1 - s) / a.KT);
+                        for (int at = 0; at < n_at; ++at) {
+                            const uint32_t ab = base + (uint32_t)at * kTileBytes;
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const uint64_t ah = sw128_desc(base + 32u * kk);
-                            if (MODE == 0) {
-                                const uint64_t al = sw128_desc(base + kTileBytes + 32u * kk);
-                                if (diag) {
-                                    mma<MODE>(d0, ah, ah, idesc, acc);
-                                    mma<MODE>(d1, ah, al, idesc, acc);
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t ah = sw128_desc(ab + 32u * kk);
+                                if (MODE == 0) {
+                                    const uint64_t al = sw128_desc(ab + plane_off + 32u * kk);
+                                    if (diag) {
+                                        mma<MODE>(d0, ah, ah, idesc, acc);
+                                        mma<MODE>(d1, ah, al, idesc, acc);
+                                    } else {
+                                        const uint64_t bh = sw128_desc(ab + tile_set + 32u * kk);
+                                        const uint64_t bl = sw128_desc(ab + tile_set + plane_off + 32u * kk);
+                                        mma<MODE>(d0, ah, bh, idesc, acc);
+                                        mma<MODE>(d0, ah, bl, idesc, 1u);
+                                        mma<MODE>(d0, al, bh, idesc, 1u);
+                                    }
                                 } else {
-                                    const uint64_t bh = sw128_desc(base + tile_set + 32u * kk);
-                                    const uint64_t bl = sw128_desc(base + tile_set + kTileBytes + 32u * kk);
-                                    mma<MODE>(d0, ah, bh, idesc, acc);
-                                    mma<MODE>(d0, ah, bl, idesc, 1u);
-                                    mma<MODE>(d0, al, bh, idesc, 1u);
+                                    const uint64_t bd = diag ? ah : sw128_desc(ab + tile_set + 32u * kk);
+                                    mma<MODE>(d0, ah, bd, idesc, acc);
                                 }
-                            } else {
-                                const uint64_t bd = diag ? ah : sw128_desc(base + tile_set + 32u * kk);
-                                mma<MODE>(d0, ah, bd, idesc, acc);
+                                acc = 1;
                             }
-                            acc = 1;
                         }
                         issued = true;
                         mma_commit(smem_u32(&empty[st]));
@@ -411,14 +427,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
     } else {
         // --------------------------------------------------------- epilogue
         // 8 warps: warp w reads TMEM lane quadrant w % 4 (rows 32q..32q+31)
-        // and one half of the Nn accumulator columns.
+        // and one half of the Nn accumulator columns.  Each warp waits for a
+        // window on its own (lane 0 polls, the warp then loads its slice) and
+        // frees the accumulator set by one arrival per warp; the 8 warps meet
+        // only at the end of an item.  A warp whose wait fails stops loading
+        // but still joins the item-end barriers, after which every warp sees
+        // the shared abort word and leaves together.
         const int et = threadIdx.x - 64;            // 0..255
         const int q = warp & 3;
         const int h = (warp - 2) >> 2;
         const int r = 32 * q + lane;
         int wi = 0;
-        bool ok = true;
-        for (int g = blockIdx.x; ok && g < a.total_items; g += gridDim.x) {
+        for (int g = blockIdx.x; g < a.total_items; g += gridDim.x) {
             const Item itm = decode_item(a, g);
             const TcModeArgs& d = a.md[itm.m];
             const bool diag = itm.b1 == itm.b2;
@@ -437,14 +457,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                 gacc[j] = 0.f;
                 tacc[j] = 0.f;
             }
+            bool dead = false;
             for (int64_t w0 = s_beg; w0 < s_end; w0 += a.W, ++wi) {
+                if (dead) continue;
                 const int b = wi & 1;
                 const uint32_t aph = (uint32_t)(wi >> 1) & 1u;
-                if (et == 0) *epi_ok = wait_bar(smem_u32(&accf[b]), aph, abort_word, a) ? 1 : 0;
-                epi_sync();
-                if (!*epi_ok) {
-                    ok = false;
-                    break;
+                int ok = 0;
+                if (lane == 0) ok = wait_bar(smem_u32(&accf[b]), aph, abort_word, a) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    dead = true;
+                    continue;
                 }
                 tc_fence_after();
                 const uint32_t trow =
@@ -460,9 +483,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                             tmem_ld_wait();
 #pragma unroll
                             for (int j = 0; j < 8; ++j) {
-                                const float wf = __uint_as_float(w[j]);
-                                gacc[8 * c + j] += __uint_as_float(v[j]) + wf;
-                                tacc[8 * c + j] += wf;
+                                gacc[8 * c + j] += __uint_as_float(v[j]);
+                                tacc[8 * c + j] += __uint_as_float(w[j]);
                             }
                         } else {
                             tmem_ld_wait();
@@ -472,66 +494,135 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                     }
                 }
                 tc_fence_before();
-                mbar_arrive(smem_u32(&acce[b]));   // this TMEM set may be refilled now
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&acce[b]));   // this warp's slice is free
             }
-            if (!ok) break;
+            epi_sync();
+            if (*abort_word) break;
             const int ldg = R2b + 1;
             if (r < R2a) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int col = col0 + 8 * c + j;
-                        if (8 * c < NH && col < R2b) Gs[r * ldg + col] = gacc[8 * c + j];
-                    }
+                for (int c = 0; c < 64; ++c) {
+                    const int col = col0 + c;
+                    if (c < NH && col < R2b) Gs[r * ldg + col] = gacc[c] + (use_t ? tacc[c] : 0.f);
+                }
             }
             epi_sync();
             if (use_t) {
                 // G[col][r] += Dhl[r][col]: each element is touched by one thread here
                 if (r < R2a) {
 #pragma unroll
-                    for (int c = 0; c < 8; ++c)
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int col = col0 + 8 * c + j;
-                            if (8 * c < NH && col < R2b) Gs[col * ldg + r] += tacc[8 * c + j];
-                        }
+                    for (int c = 0; c < 64; ++c) {
+                        const int col = col0 + c;
+                        if (c < NH && col < R2b) Gs[col * ldg + r] += tacc[c];
+                    }
                 }
                 epi_sync();
             }
             const float gs = MODE == 0 ? 1.0f / (kSplitScale * kSplitScale) : 1.0f;
             const int N = d.N, C = d.C, P = d.P;
             const int npl = diag ? nb1 * (nb1 + 1) / 2 : nb1 * nb2;
-            int li = 0;
-            int row_next = nb1;                     // triangle: first index of row li + 1
-            for (int pl = et; pl < npl; pl += 256) {
-                int lj;
-                if (diag) {
-                    while (pl >= row_next) {
-                        ++li;
-                        row_next += nb1 - li;
+            const bool direct = d.n_split == 1;
+            {
+                // kVB pairs per thread at a time: their accumulator loads are
+                // issued together, so their latencies overlap
+                int li = 0;
+                int row_next = nb1;                 // triangle: first index of row li + 1
+                for (int base = et; base < npl; base += kVB * 256) {
+                    int pp[kVB];
+                    float vre[kVB], vim[kVB];
+#pragma unroll
+                    for (int u = 0; u < kVB; ++u) {
+                        const int pl = base + 256 * u;
+                        pp[u] = -1;
+                        vre[u] = vim[u] = 0.f;
+                        if (pl < npl) {
+                            int lj;
+                            if (diag) {
+                                while (pl >= row_next) {
+                                    ++li;
+                                    row_next += nb1 - li;
+                                }
+                                lj = li + (pl - (row_next - (nb1 - li)));
+                            } else {
+                                li = pl / nb2;
+                                lj = pl - li * nb2;
+                            }
+                            const float re = Gs[li * ldg + lj] + Gs[(nb1 + li) * ldg + nb2 + lj];
+                            const float im = Gs[(nb1 + li) * ldg + lj] - Gs[li * ldg + nb2 + lj];
+                            const int i = 64 * itm.b1 + li;
+                            const int j = 64 * itm.b2 + lj;
+                            float f = gs;
+                            if (MODE != 0)
+                                f = 1.0f / (__ldg(d.scale + (int64_t)i * C + itm.k) *
+                                            __ldg(d.scale + (int64_t)j * C + itm.k));
+                            pp[u] = i * N - i * (i - 1) / 2 + (j - i);
+                            vre[u] = re * f;
+                            vim[u] = im * f;
+                        }
                     }
-                    lj = li + (pl - (row_next - (nb1 - li)));
-                } else {
-                    li = pl / nb2;
-                    lj = pl - li * nb2;
+                    if (direct) {
+                        double2 old[kVB];
+#pragma unroll
+                        for (int u = 0; u < kVB; ++u)
+                            if (pp[u] >= 0) old[u] = __ldcg(d.acc + (int64_t)itm.k * P + pp[u]);
+#pragma unroll
+                        for (int u = 0; u < kVB; ++u)
+                            if (pp[u] >= 0)       // sole owner of (k, p) in this launch
+                                d.acc[(int64_t)itm.k * P + pp[u]] =
+                                    make_double2(old[u].x + (double)vre[u], old[u].y + (double)vim[u]);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < kVB; ++u)
+                            if (pp[u] >= 0)
+                                d.partial[((int64_t)itm.sp * C + itm.k) * P + pp[u]] =
+                                    make_float2(vre[u], vim[u]);
+                    }
                 }
-                const float re = Gs[li * ldg + lj] + Gs[(nb1 + li) * ldg + nb2 + lj];
-                const float im = Gs[(nb1 + li) * ldg + lj] - Gs[li * ldg + nb2 + lj];
-                const int i = 64 * itm.b1 + li;
-                const int j = 64 * itm.b2 + lj;
-                const int p = i * N - i * (i - 1) / 2 + (j - i);
-                float f = gs;
-                if (MODE != 0)
-                    f = 1.0f / (__ldg(d.scale + (int64_t)i * C + itm.k) * __ldg(d.scale + (int64_t)j * C + itm.k));
-                if (d.acc) {
-                    double2* dst = d.acc + (int64_t)itm.k * P + p;   // sole owner of (k, p) here
-                    double2 v = *dst;
-                    v.x += (double)(re * f);
-                    v.y += (double)(im * f);
-                    *dst = v;
-                } else {
-                    d.partial[((int64_t)itm.sp * C + itm.k) * P + p] = make_float2(re * f, im * f);
+            }
+            if (!direct) {
+                // The last of the n_split items of this (channel, block pair) to
+                // finish adds every partial, in split order, into the FP64
+                // accumulator: deterministic, and no reduction launch.
+                __threadfence();
+                epi_sync();
+                if (et == 0) {
+                    const int old = atomicAdd(d.ticket + itm.k * d.npairs + itm.pr, 1);
+                    *epi_last = old == d.n_split - 1 ? 1 : 0;
+                }
+                epi_sync();
+                if (*epi_last) {
+                    __threadfence();
+                    int li = 0;
+                    int row_next = nb1;
+                    for (int pl = et; pl < npl; pl += 256) {
+                        int lj;
+                        if (diag) {
+                            while (pl >= row_next) {
+                                ++li;
+                                row_next += nb1 - li;
+                            }
+                            lj = li + (pl - (row_next - (nb1 - li)));
+                        } else {
+                            li = pl / nb2;
+                            lj = pl - li * nb2;
+                        }
+                        const int i = 64 * itm.b1 + li;
+                        const int j = 64 * itm.b2 + lj;
+                        const int p = i * N - i * (i - 1) / 2 + (j - i);
+                        double re = 0.0, im = 0.0;
+                        for (int sp = 0; sp < d.n_split; ++sp) {
+                            const float2 v = __ldcg(d.partial + ((int64_t)sp * C + itm.k) * P + p);
+                            re += (double)v.x;
+                            im += (double)v.y;
+                        }
+                        double2* dst = d.acc + (int64_t)itm.k * P + p;
+                        double2 v = *dst;
+                        v.x += re;
+                        v.y += im;
+                        *dst = v;
+                    }
+                    if (et == 0) d.ticket[itm.k * d.npairs + itm.pr] = 0;
                 }
             }
             epi_sync();
@@ -578,11 +669,14 @@ struct TcPlan {
     bool have_map = false;
     int64_t cap = 0;
     int max_split = 1;
-    int window = 0;           // 0 = kDefaultWindow
+    int window = 0;           // 0 = per-mode default
     int stages = 0;           // 0 = as many as shared memory allows
+    int split = 0;            // 0 = planner's choice
+    int atoms = 0;            // k-tiles per stage, 0 = automatic
     unsigned long long timeout_ns = 4000000000ull;
     int withhold = 0;                    // test hook for the next launch
     unsigned long long hook_timeout_ns = 0;
+    int* ticket = nullptr;               // [C][npairs] arrival counters
     // split decisions already made, keyed by the S_pad of every mode in the launch
     std::vector<std::pair<std::vector<int64_t>, std::vector<int>>> split_cache;
 };
@@ -609,8 +703,23 @@ int tc_plan_create(TcPlan** out, int N, int C, int spec_type, std::string& err) 
         err = "cudaDeviceGetAttribute failed";
         return CORR_ECUDA;
     }
+    const size_t tb = (size_t)p->C * p->npairs * sizeof(int);
+    if (cudaMalloc((void**)&p->ticket, tb) != cudaSuccess || cudaMemset(p->ticket, 0, tb) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p->ticket);
+        delete p;
+        err = "device allocation failed";
+        return CORR_ENOMEM;
+    }
     *out = p;
     return CORR_OK;
+}
+
+int tc_reset(TcPlan* p) {
+    // after an aborted launch some arrival counters may be left non-zero
+    return cudaMemset(p->ticket, 0, (size_t)p->C * p->npairs * sizeof(int)) == cudaSuccess
+               ? CORR_OK
+               : CORR_ECUDA;
 }
 
 int tc_plan_update(TcPlan* p, void* spec, int64_t cap, int N, int C, int spec_type,
@@ -641,7 +750,15 @@ int tc_plan_update(TcPlan* p, void* spec, int64_t cap, int N, int C, int spec_ty
     return CORR_OK;
 }
 
-int tc_set_tiles(TcPlan* p, int window, int stages, std::string& err) {
+int tc_set_tiles(TcPlan* p, int window, int stages, int split, int atoms, std::string& err) {
+    if (atoms < 0 || atoms > 4) {
+        err = "atoms must be in [0, 4]";
+        return CORR_EINVAL;
+    }
+    if (split < 0 || split > 64) {
+        err = "split must be in [0, 64]";
+        return CORR_EINVAL;
+    }
     if (window != 0 && (window < p->KT || window % p->KT || window > 4096)) {
         err = "window must be a multiple of the k-tile (64 spectra, 128 for FP8) up to 4096";
         return CORR_EINVAL;
@@ -652,13 +769,16 @@ int tc_set_tiles(TcPlan* p, int window, int stages, std::string& err) {
     }
     p->window = window;
     p->stages = stages;
+    p->split = split;
+    p->atoms = atoms;
+    p->split_cache.clear();
     return CORR_OK;
 }
 
 namespace {
 
 struct LaunchShape {
-    int two_tiles, gs_floats, stages, W;
+    int two_tiles, gs_floats, stages, W, atoms;
     size_t smem;
 };
 
@@ -670,12 +790,32 @@ LaunchShape launch_shape(TcPlan* const* plans, int n) {
         r2max = std::max(r2max, 2 * std::min(64, plans[m]->N));
     }
     L.gs_floats = r2max * (r2max + 1);
-    const size_t stage_bytes = (size_t)plans[0]->planes * kTileBytes * (L.two_tiles ? 2 : 1);
     const size_t fixed = 1024 + (size_t)L.gs_floats * 4 + 16 + 16 + 8 * (2 * 16 + 5);
-    int smax = (int)((kSmemBudget - fixed) / stage_bytes);
-    smax = std::min(smax, 16);
+    auto fit = [&](int atoms) {
+        const size_t sb = (size_t)plans[0]->planes * atoms * kTileBytes * (L.two_tiles ? 2 : 1);
+        return std::min<int>(16, (int)((kSmemBudget - fixed) / sb));
+    };
+    // k-tiles per stage: as many (up to 4) as still leave 3 stages, unless set
+    L.atoms = plans[0]->atoms;
+    if (!L.atoms) {
+        L.atoms = 1;
+        for (int at = 4; at > 1; at /= 2)
+            if (fit(at) >= 3) {
+                L.atoms = at;
+                break;
+            }
+    }
+    while (L.atoms > 1 && fit(L.atoms) < 2) L.atoms /= 2;
+    const size_t stage_bytes =
+        (size_t)plans[0]->planes * L.atoms * kTileBytes * (L.two_tiles ? 2 : 1);
+    const int smax = fit(L.atoms);
     L.stages = plans[0]->stages ? std::min(plans[0]->stages, smax) : std::min(smax, 8);
-    L.W = plans[0]->window ? plans[0]->window : std::max(kDefaultWindow, plans[0]->KT);
+    const int step = plans[0]->KT * L.atoms;
+    // default window: 256 spectra in FP32 mode (TMEM accumulation bias ~1e-6
+    // at full size), 512 for FP16 / FP8 (their input rounding dominates)
+    const int W0 = plans[0]->mode == 0 ? 256 : 512;
+    int W = plans[0]->window ? plans[0]->window : std::max(W0, plans[0]->KT);
+    L.W = (W + step - 1) / step * step;   // windows hold whole stages
     L.smem = fixed + (size_t)L.stages * stage_bytes;
     return L;
 }
@@ -686,6 +826,15 @@ LaunchShape launch_shape(TcPlan* const* plans, int n) {
 // epilogue then accumulates in FP64 directly and no reduction is launched).
 std::vector<int> choose_splits(TcPlan* const* plans, int n, const int64_t* S_pad) {
     std::vector<int64_t> key(S_pad, S_pad + n);
+    if (plans[0]->split > 0) {
+        // fixed by corr_set_tiles: ranges per channel, at most one per k-tile
+        std::vector<int> fixed(n);
+        for (int m = 0; m < n; ++m) {
+            const int64_t tiles = std::max<int64_t>(1, S_pad[m] / plans[m]->KT);
+            fixed[m] = (int)std::min<int64_t>(std::min(plans[0]->split, plans[m]->max_split), tiles);
+        }
+        return fixed;
+    }
     auto& cache = plans[0]->split_cache;
     for (auto& e : cache)
         if (e.first == key) return e.second;
@@ -715,13 +864,15 @@ std::vector<int> choose_splits(TcPlan* const* plans, int n, const int64_t* S_pad
             for (int s = 0; s < sp[m]; ++s) {
                 const int64_t t = std::min<int64_t>(per, tiles - (int64_t)s * per);
                 for (int pr = 0; pr < p->npairs; ++pr) {
-                    const double w = (double)t * (p->nblk > 1 ? 1.5 : 1.0) + 2.0;
+                    // cost in k-tiles: the tiles, plus the end of an item (~4 k-tiles
+                    // measured on GB300) and the in-kernel combine of split partials
+                    const double w = (double)t * (p->nblk > 1 ? 1.5 : 1.0) + 4.0 + (sp[m] > 1 ? 2.0 : 0.0);
                     for (int k = 0; k < p->C; ++k, ++g) load[g % sms] += w;
                 }
             }
         }
         double score = *std::max_element(load.begin(), load.end());
-        if (needs_reduce) score *= 1.15;
+        (void)needs_reduce;
         if (score < best_score - 1e-9) {
             best_score = score;
             best = sp;
@@ -759,6 +910,7 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
     a.stages = L.stages;
     a.KT = plans[0]->KT;
     a.W = L.W;
+    a.atoms = L.atoms;
     a.two_tiles = L.two_tiles;
     a.gs_floats = L.gs_floats;
     a.status = runs[0].status;
@@ -787,10 +939,11 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
         d.n_items = d.n_split * p->npairs * p->C;
         base += d.n_items;
         d.partial = runs[m].partial;
-        d.acc = d.n_split == 1 ? runs[m].acc : nullptr;
+        d.acc = runs[m].acc;
+        d.ticket = plans[m]->ticket;
         d.scale = runs[m].scale;
         runs[m].n_split = d.n_split;
-        runs[m].direct = d.acc != nullptr || d.n_split == 0;
+        runs[m].direct = true;          // splits are combined inside the kernel
     }
     a.total_items = base;
     if (base == 0) return CORR_OK;
@@ -827,6 +980,10 @@ int tc_test_withhold(TcPlan* p, double wait_limit_s, std::string& err) {
     return CORR_OK;
 }
 
-void tc_plan_destroy(TcPlan* p) { delete p; }
+void tc_plan_destroy(TcPlan* p) {
+    if (!p) return;
+    cudaFree(p->ticket);
+    delete p;
+}
 
 }  // namespace gbcorr

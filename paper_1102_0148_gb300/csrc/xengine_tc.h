@@ -18,7 +18,7 @@ struct TcRun {
     double2* acc;             // [C][P] FP64 accumulator, added to when n_split == 1
     const float* scale;       // [N][C] pre-cast scales (FP16 / FP8), else nullptr
     int* status;              // device status word (bounded waits)
-    int n_split;              // out: ranges per channel
+    int n_split;              // out: ranges per channel (combined in the kernel)
     bool direct;              // out: accumulated into acc (no reduction needed)
 };
 
@@ -26,9 +26,10 @@ struct TcRun {
 int tc_plan_create(TcPlan** out, int N, int C, int spec_type, std::string& err);
 // (Re)bind the plan to a workspace of `cap` frames per row.
 int tc_plan_update(TcPlan* p, void* spec, int64_t cap, int N, int C, int spec_type, std::string& err);
-// Tile choices: TMEM accumulation window (spectra, 0 = default) and
-// pipeline stages (0 = as many as shared memory holds, up to 8).
-int tc_set_tiles(TcPlan* p, int window, int stages, std::string& err);
+// Tile choices: TMEM accumulation window (spectra, 0 = default), pipeline
+// stages (0 = as many as shared memory holds, up to 8), ranges per channel
+// of a pass (0 = the planner's choice) and k-tiles per stage (0 = automatic).
+int tc_set_tiles(TcPlan* p, int window, int stages, int split, int atoms, std::string& err);
 // One persistent launch over the passes of n plans sharing a precision.
 // Modes whose run reports direct = false need the reduction of their
 // n_split partial blocks into acc.
@@ -36,6 +37,8 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
 // Test hook: the next launch's CTA 0 skips the copy of its first k-tile, so
 // its MMA thread's bounded wait expires after wait_limit_s.
 int tc_test_withhold(TcPlan* p, double wait_limit_s, std::string& err);
+// Clear the split arrival counters (after an aborted launch).
+int tc_reset(TcPlan* p);
 void tc_plan_destroy(TcPlan* p);
 
 }  // namespace gbcorr

@@ -25,6 +25,7 @@ import os
 WINDOWS = {"fp32": (64, 128, 256), "fp16": (64, 128, 256, 512), "fp8": (128, 256, 512)}
 STAGES = (2, 3, 4, 6, 8)
 CHUNKS = (1024, 2048, 4096)
+SPLITS = (0, 1, 2, 4)
 
 
 def cache_path():
@@ -75,7 +76,7 @@ def apply(c, N, K, dtype):
     if not t:
         return False
     corr.corr_set_chunk(c.h, t["chunk"])
-    corr.corr_set_tiles(c.h, t["window"], t["stages"])
+    corr.corr_set_tiles(c.h, t["window"], t["stages"], t.get("split", 0))
     return True
 
 
@@ -84,7 +85,7 @@ def apply_batch(b, modes, dtype):
     t = _load().get(key_batch(modes, dtype))
     if not t:
         return False
-    corr.corr_batch_set_tiles(b.b, t["window"], t["stages"])
+    corr.corr_batch_set_tiles(b.b, t["window"], t["stages"], t.get("split", 0))
     return True
 
 
@@ -103,8 +104,8 @@ def _time(fn, repeats, stream):
 
 
 def tune(N, K, dtype="fp32", frames=8192, repeats=3, save=True, windows=None, stages=None,
-         chunks=None):
-    """Sweep (chunk, window, stages) for one correlator; returns the best."""
+         chunks=None, splits=None):
+    """Sweep (chunk, window, stages, split) for one correlator; returns the best."""
     import torch
     from . import corr, synth
     dev, _ = synth.make_samples_torch(N, frames * K, K, seed=7, device="cuda")
@@ -113,10 +114,11 @@ def tune(N, K, dtype="fp32", frames=8192, repeats=3, save=True, windows=None, st
     P, C = N * (N + 1) // 2, K // 2
     vis = torch.empty((P, C), dtype=torch.complex64, device="cuda")
     best, results = None, []
-    for ch, w, st in itertools.product(chunks or CHUNKS, windows or WINDOWS[dtype], stages or STAGES):
+    for ch, w, st, sp in itertools.product(chunks or CHUNKS, windows or WINDOWS[dtype],
+                                           stages or STAGES, splits or SPLITS):
         try:
             with corr.Correlator(N, K, dtype, chunk=ch, stream=stream.cuda_stream) as c:
-                corr.corr_set_tiles(c.h, w, st)
+                corr.corr_set_tiles(c.h, w, st, sp)
 
                 def step():
                     corr.corr_push(c.h, dev, frames * K)
@@ -125,10 +127,10 @@ def tune(N, K, dtype="fp32", frames=8192, repeats=3, save=True, windows=None, st
                 ms = _time(step, repeats, stream)
         except corr.CorrError:
             continue
-        results.append((ms, ch, w, st))
+        results.append((ms, ch, w, st, sp))
         if best is None or ms < best[0]:
-            best = (ms, ch, w, st)
-    out = {"chunk": best[1], "window": best[2], "stages": best[3], "ms": best[0],
+            best = (ms, ch, w, st, sp)
+    out = {"chunk": best[1], "window": best[2], "stages": best[3], "split": best[4], "ms": best[0],
            "spectra_per_s": frames / (best[0] * 1e-3), "frames": frames,
            "candidates": len(results)}
     if save:
@@ -136,8 +138,9 @@ def tune(N, K, dtype="fp32", frames=8192, repeats=3, save=True, windows=None, st
     return out
 
 
-def tune_batch(modes, dtype="fp32", T=1 << 22, repeats=3, save=True, windows=None, stages=None):
-    """Sweep (window, stages) for a batch, timing replays of its graph."""
+def tune_batch(modes, dtype="fp32", T=1 << 22, repeats=3, save=True, windows=None, stages=None,
+               splits=None):
+    """Sweep (window, stages, split) for a batch, timing replays of its graph."""
     import torch
     from . import corr, synth
     data = []
@@ -147,21 +150,23 @@ def tune_batch(modes, dtype="fp32", T=1 << 22, repeats=3, save=True, windows=Non
     vis = [torch.empty((N * (N + 1) // 2, K // 2), dtype=torch.complex64, device="cuda")
            for N, K in modes]
     best, results = None, []
-    for w, st in itertools.product(windows or WINDOWS[dtype], stages or STAGES):
+    for w, st, sp in itertools.product(windows or WINDOWS[dtype], stages or STAGES,
+                                       splits or SPLITS):
         try:
             with corr.CorrelatorBatch(modes, dtype) as b:
                 for h, (N, K) in zip(b.handles, modes):
                     corr.corr_set_chunk(h, T // K)       # one pass per mode and push
-                corr.corr_batch_set_tiles(b.b, w, st)
+                corr.corr_batch_set_tiles(b.b, w, st, sp)
                 b.capture(data, vis)
                 s = torch.cuda.ExternalStream(b.stream)
                 ms = _time(b.replay, repeats, s)
         except corr.CorrError:
             continue
-        results.append((ms, w, st))
+        results.append((ms, w, st, sp))
         if best is None or ms < best[0]:
-            best = (ms, w, st)
-    out = {"window": best[1], "stages": best[2], "ms": best[0], "samples_per_antenna": T,
+            best = (ms, w, st, sp)
+    out = {"window": best[1], "stages": best[2], "split": best[3], "ms": best[0],
+           "samples_per_antenna": T,
            "candidates": len(results)}
     if save:
         _save(key_batch(modes, dtype), out)

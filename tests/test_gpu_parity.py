@@ -244,13 +244,13 @@ def test_n256_k1024(lib, torch_cuda, dtype):
     assert vis_error(V, R, N) <= TOL
 
 
-@pytest.mark.parametrize("window,stages", [(64, 2), (256, 3), (512, 0)])
-def test_tile_choices_keep_parity(lib, torch_cuda, window, stages):
+@pytest.mark.parametrize("window,stages,split", [(64, 2, 0), (256, 3, 8), (512, 0, 3), (128, 4, 1)])
+def test_tile_choices_keep_parity(lib, torch_cuda, window, stages, split):
     N, K, S = 44, 512, 600
     packed, _ = synth.make_samples(N, S * K, K, seed=SEED + 21)
     R, _ = oracle.correlate(packed, N, K)
     with lib.Correlator(N, K, "fp32") as c:
-        lib.corr_set_tiles(c.h, window, stages)
+        lib.corr_set_tiles(c.h, window, stages, split)
         c.push(torch_cuda.from_numpy(packed.reshape(-1)).cuda(), S * K)
         V, n = c.dump(fp64=True)
     assert vis_error(V, R, N) <= TOL

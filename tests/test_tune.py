@@ -34,8 +34,8 @@ def test_tune_and_apply_keep_parity(lib, tmp_path, monkeypatch):
     monkeypatch.setenv("GBCORR_TUNE_CACHE", str(tmp_path / "t.json"))
     N, K = 12, 512
     best = tune.tune(N, K, "fp32", frames=512, repeats=1, windows=(64, 128), stages=(2, 4),
-                     chunks=(256, 512))
-    assert best["candidates"] == 8 and best["ms"] > 0
+                     chunks=(256, 512), splits=(0, 2))
+    assert best["candidates"] == 16 and best["ms"] > 0
     S = 300
     packed, _ = synth.make_samples(N, S * K, K, seed=99)
     R, _ = oracle.correlate(packed, N, K)
@@ -54,7 +54,8 @@ def test_tune_and_apply_keep_parity(lib, tmp_path, monkeypatch):
 def test_tune_batch(lib, tmp_path, monkeypatch):
     monkeypatch.setenv("GBCORR_TUNE_CACHE", str(tmp_path / "t.json"))
     modes = [(44, 512), (11, 4096)]
-    best = tune.tune_batch(modes, "fp16", T=1 << 16, repeats=1, windows=(64, 128), stages=(3,))
+    best = tune.tune_batch(modes, "fp16", T=1 << 16, repeats=1, windows=(64, 128), stages=(3,),
+                           splits=(1,))
     assert best["candidates"] == 2
     with lib.CorrelatorBatch(modes, "fp16") as b:
         assert tune.apply_batch(b, modes, "fp16")

@@ -519,6 +519,202 @@ __global__ void __launch_bounds__(kF1024Threads, 2) fengine_k1024(FengineArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// K = 512 R F-engine for R = 4, 8 (K = 2048, 4096): a group of B = 16 R
+// threads per spectrum, 16 complex points per thread.
+//
+// With L = K/2 = 256 R, n = t + B j, t = r + R u (r < R, u < 16) and
+// k = k1 + 16 k2 + 256 k3 (k1, k2 < 16, k3 < R):
+//   X1[t][k1] = W_L^{t k1} sum_j z[t + B j] W16^{j k1}
+//   Z[k]      = sum_r W_R^{r k3} W_B^{r k2} sum_u W16^{u k2} X1[r + R u][k1].
+// Thread t does the first 16-point DFT; after an exchange through shared
+// memory thread (k1 = t mod 16, r = t / 16) does the second over u, and after
+// a second exchange the R-point DFTs over r for its Q = 16/R values of k2.  Z
+// goes back to shared memory in natural order, where the real split reads
+// Z[k] and Z[L-k].  Each group syncs on its own named barrier; the CTA
+// stages 2 G frames (G groups, two rounds) and writes them as runs of the
+// workspace rows like the kernels above.  The exchange strides (B + 1 and 17
+// complex) keep every half-warp on distinct banks.
+// ---------------------------------------------------------------------------
+
+constexpr int kRadThreads = 512;
+
+__device__ __forceinline__ void group_bar(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// 8-point forward DFT in place (radix 2 x 4).
+__device__ __forceinline__ void dft8(float2& x0, float2& x1, float2& x2, float2& x3, float2& x4,
+                                     float2& x5, float2& x6, float2& x7) {
+    constexpr float r2 = 0.707106781186547524f;
+    dft4(x0, x2, x4, x6);                         // E[0..3] in x0, x2, x4, x6
+    dft4(x1, x3, x5, x7);                         // O[0..3] in x1, x3, x5, x7
+    const float2 o1 = make_float2(r2 * (x3.x + x3.y), r2 * (x3.y - x3.x));    // W8^1 O1
+    const float2 o2 = cmi(x5);                                                // W8^2 O2
+    const float2 o3 = make_float2(r2 * (x7.y - x7.x), -r2 * (x7.x + x7.y));   // W8^3 O3
+    const float2 e0 = x0, e1 = x2, e2 = x4, e3 = x6, o0 = x1;
+    x0 = cadd(e0, o0);
+    x4 = csub(e0, o0);
+    x1 = cadd(e1, o1);
+    x5 = csub(e1, o1);
+    x2 = cadd(e2, o2);
+    x6 = csub(e2, o2);
+    x3 = cadd(e3, o3);
+    x7 = csub(e3, o3);
+}
+
+template <int R>
+__device__ __forceinline__ void dft_r(float2 (&v)[R]) {
+    if constexpr (R == 4) {
+        dft4(v[0], v[1], v[2], v[3]);
+    } else {
+        static_assert(R == 8, "radix");
+        dft8(v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]);
+    }
+}
+
+template <int R>
+struct Rad16Shape {
+    static constexpr int L = 256 * R;
+    static constexpr int B = 16 * R;                  // threads per spectrum
+    static constexpr int Q = 16 / R;
+    static constexpr int G = kRadThreads / B;         // spectra in flight per CTA
+    static constexpr int FT = 2 * G;                  // frames per CTA
+    static constexpr int M = FT / 4;                  // lanes per row in the store
+    static constexpr int SR = 2 * L + 8 / M;          // staging row stride (floats)
+    static constexpr int STG = (FT * SR + 3) & ~3;    // staging floats
+    static constexpr int XB = 272 * R;                // exchange complex per group
+    static size_t smem(bool dbg) {
+        return (size_t)(dbg ? 0 : STG) * sizeof(float) +
+               ((size_t)G * XB + 16 * B + 16 * R) * sizeof(float2);
+    }
+};
+
+template <int R, int OUT>
+__global__ void __launch_bounds__(kRadThreads, 1) fengine_rad16(FengineArgs a) {
+    constexpr bool DEBUG = OUT == kOutDebug;
+    using Sh = Rad16Shape<R>;
+    constexpr int L = Sh::L, B = Sh::B, Q = Sh::Q, G = Sh::G, FT = Sh::FT, M = Sh::M,
+                  SR = Sh::SR, XB = Sh::XB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* stg = reinterpret_cast<float*>(smem_raw);                            // [FT][SR]
+    float2* xbuf = reinterpret_cast<float2*>(stg + (DEBUG ? 0 : Sh::STG));      // [G][XB]
+    float2* tw1 = xbuf + G * XB;                                                // [16 k1][B t]
+    float2* tw2 = tw1 + 16 * B;                                                 // [R r][16 k2]
+
+    const int tid = threadIdx.x;
+    const int g = tid / B;
+    const int t = tid - g * B;
+    const int i = blockIdx.y;
+    const int64_t s0 = (int64_t)blockIdx.x * FT;
+    const float post = OUT == SPEC_F16X2 ? kSplitScale : 1.0f;
+    const float chalf = 0.5f * post;
+
+    // W_L^{t k1} = W_K^{2 t k1 mod K};  W_B^{r k2} = W_K^{32 r k2}
+    for (int e = tid; e < 16 * B; e += kRadThreads) {
+        const int kk = e / B, tt = e - kk * B;
+        tw1[e] = a.twiddle[(2 * tt * kk) & (2 * L - 1)];
+    }
+    for (int e = tid; e < 16 * R; e += kRadThreads) tw2[e] = a.twiddle[32 * (e >> 4) * (e & 15)];
+
+    uint4 raw0 = make_uint4(0u, 0u, 0u, 0u), raw1 = raw0;
+    {
+        const int64_t sa = s0 + g, sb = sa + G;
+        if (sa < a.S) raw0 = __ldg(reinterpret_cast<const uint4*>(a.in + (sa * a.N + i) * L) + t);
+        if (sb < a.S) raw1 = __ldg(reinterpret_cast<const uint4*>(a.in + (sb * a.N + i) * L) + t);
+    }
+    __syncthreads();
+
+    float2* xb = xbuf + g * XB;
+    const unsigned char* xbytes = reinterpret_cast<const unsigned char*>(xb);
+    const int bar = 1 + g;
+    const int k1 = t & 15, r = t >> 4;
+
+#pragma unroll 1
+    for (int rd = 0; rd < 2; ++rd) {
+        const int f = g + G * rd;
+        const int64_t s = s0 + f;
+        *reinterpret_cast<uint4*>(xb + 2 * t) = rd == 0 ? raw0 : raw1;
+        group_bar(bar, B);
+        float2 x[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const unsigned b = xbytes[t + B * j];
+            x[j] = make_float2(nib_lo(b), nib_hi(b));
+        }
+        group_bar(bar, B);
+        dft16(x);
+#pragma unroll
+        for (int q = 1; q < 16; ++q) x[q] = cmul(x[q], tw1[q * B + t]);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) xb[q * (B + 1) + t] = x[q];
+        group_bar(bar, B);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) x[u] = xb[k1 * (B + 1) + r + R * u];
+        group_bar(bar, B);
+        dft16(x);
+#pragma unroll
+        for (int q = 1; q < 16; ++q) x[q] = cmul(x[q], tw2[r * 16 + q]);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) xb[k1 + 17 * (q * R + r)] = x[q];
+        group_bar(bar, B);
+#pragma unroll
+        for (int qq = 0; qq < Q; ++qq) {
+            float2 v[R];
+#pragma unroll
+            for (int rp = 0; rp < R; ++rp) v[rp] = xb[k1 + 17 * ((r * Q + qq) * R + rp)];
+            dft_r<R>(v);
+#pragma unroll
+            for (int k3 = 0; k3 < R; ++k3) x[qq * R + k3] = v[k3];
+        }
+        group_bar(bar, B);
+        // x[qq R + k3] = Z[k1 + 16 (r Q + qq) + 256 k3]
+#pragma unroll
+        for (int qq = 0; qq < Q; ++qq)
+#pragma unroll
+            for (int k3 = 0; k3 < R; ++k3) xb[k1 + 16 * (r * Q + qq) + 256 * k3] = x[qq * R + k3];
+        group_bar(bar, B);
+#pragma unroll 4
+        for (int m = 0; m < 16; ++m) {
+            const int k = t + B * m;
+            const float2 zk = xb[k], zc = xb[(L - k) & (L - 1)];
+            const float2 w = __ldg(a.twiddle + k);
+            const float2 wp = make_float2(0.5f * post * w.y, -0.5f * post * w.x);
+            const float2 S = make_float2(zk.x + zc.x, zk.y - zc.y);
+            const float2 D = make_float2(zk.x - zc.x, zk.y + zc.y);
+            const float2 wd = cmul(wp, D);
+            float2 X = make_float2(fmaf(chalf, S.x, wd.x), fmaf(chalf, S.y, wd.y));
+            if (a.corr) X = cmul(__ldg(a.corr + (int64_t)i * L + k), X);
+            if (DEBUG) {
+                if (s < a.S) a.debug_out[((int64_t)i * a.S + s) * L + k] = X;
+            } else {
+                if (OUT == SPEC_F16 || OUT == SPEC_F8) {
+                    const float sc = __ldg(a.scale + (int64_t)i * L + k);
+                    X.x *= sc;
+                    X.y *= sc;
+                }
+                stg[f * SR + k] = X.x;
+                stg[f * SR + L + k] = X.y;
+            }
+        }
+        group_bar(bar, B);
+    }
+    if (DEBUG) return;
+    __syncthreads();
+    // 2L workspace rows (plane, k) x FT frames: M lanes per row, 4 frames each
+    const int l32 = tid & 31, warp = tid >> 5;
+    const int m = l32 % M;
+    constexpr int RPW = 32 / M;
+    if (s0 + 4 * m >= a.S_pad) return;
+    for (int row = RPW * warp + l32 / M; row < 2 * L; row += RPW * (kRadThreads / 32)) {
+        const int plane = row / L;
+        const int k = row - plane * L;
+        const float* src = stg + 4 * m * SR + row;
+        const int64_t off = ((int64_t)k * 2 * a.N + spec_row(plane, i, a.N)) * a.ld + s0 + 4 * m;
+        store4<OUT>(a.spec, off, a.plane_stride, src[0], src[SR], src[2 * SR], src[3 * SR]);
+    }
+}
+
 __global__ void correction_table_kernel(const float2* g, const float* tau, int N, int K,
                                         float2* out) {
     const int C = K / 2;
@@ -584,6 +780,36 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
             case SPEC_F8: return go(fengine_k1024<SPEC_F8>);
             default: return go(fengine_k1024<SPEC_F16X2>);
         }
+    }
+    if ((a.K == 2048 || a.K == 4096) && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0) {
+        const int64_t fr = dbg ? a.S : a.S_pad;
+        if (fr <= 0) return cudaSuccess;
+        auto go = [&](auto kern, int FT, size_t smem) -> cudaError_t {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+            dim3 grid((unsigned)((fr + FT - 1) / FT), (unsigned)a.N);
+            kern<<<grid, kRadThreads, smem, st>>>(a);
+            return cudaGetLastError();
+        };
+        auto pick = [&](auto shape, auto k_dbg, auto k_f32, auto k_f16, auto k_f8, auto k_x2) {
+            using Sh = decltype(shape);
+            const size_t sm = Sh::smem(dbg);
+            if (dbg) return go(k_dbg, Sh::FT, sm);
+            switch (a.spec_type) {
+                case SPEC_F32: return go(k_f32, Sh::FT, sm);
+                case SPEC_F16: return go(k_f16, Sh::FT, sm);
+                case SPEC_F8: return go(k_f8, Sh::FT, sm);
+                default: return go(k_x2, Sh::FT, sm);
+            }
+        };
+        if (a.K == 2048)
+            return pick(Rad16Shape<4>{}, fengine_rad16<4, kOutDebug>, fengine_rad16<4, SPEC_F32>,
+                        fengine_rad16<4, SPEC_F16>, fengine_rad16<4, SPEC_F8>,
+                        fengine_rad16<4, SPEC_F16X2>);
+        return pick(Rad16Shape<8>{}, fengine_rad16<8, kOutDebug>, fengine_rad16<8, SPEC_F32>,
+                    fengine_rad16<8, SPEC_F16>, fengine_rad16<8, SPEC_F8>,
+                    fengine_rad16<8, SPEC_F16X2>);
     }
     int FT = 8192 / C;
     FT = FT < 1 ? 1 : (FT > 32 ? 32 : FT);

@@ -114,19 +114,44 @@ __global__ void reduce_partials_kernel(const float2* part, int n_split, int64_t 
     }
 }
 
-__global__ void dump_kernel(double2* acc, int C, int P, void* vis, int fp64) {
-    const int64_t total = (int64_t)C * P;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int p = (int)(e / C);
-        const int k = (int)(e - (int64_t)p * C);
-        const int64_t src = (int64_t)k * P + p;
-        const double2 v = acc[src];
-        acc[src] = make_double2(0.0, 0.0);
-        if (fp64)
-            static_cast<double2*>(vis)[e] = v;
-        else
-            static_cast<float2*>(vis)[e] = make_float2((float)v.x, (float)v.y);
+// acc [C][P] -> vis [P][C] through 32 x 32 shared-memory tiles, so both the
+// reads (along p) and the writes (along k) are coalesced; acc is cleared.
+constexpr int kDT = 32;
+
+__global__ void __launch_bounds__(kDT * 8) dump_kernel(double2* __restrict__ acc, int C, int P,
+                                                     void* __restrict__ vis, int fp64) {
+    __shared__ double2 tile[kDT][kDT + 1];
+    const int p0 = blockIdx.x * kDT;
+    const int k0 = blockIdx.y * kDT;
+    const int tx = threadIdx.x & (kDT - 1);
+    const int ty = threadIdx.x / kDT;               // 0..7
+    // all four loads in flight before the clearing stores
+    double2 v[kDT / 8];
+    const int p = p0 + tx;
+#pragma unroll
+    for (int q = 0; q < kDT / 8; ++q) {
+        const int k = k0 + ty + 8 * q;
+        v[q] = (k < C && p < P) ? acc[(int64_t)k * P + p] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int q = 0; q < kDT / 8; ++q) {
+        const int k = k0 + ty + 8 * q;
+        if (k < C && p < P) acc[(int64_t)k * P + p] = make_double2(0.0, 0.0);
+        tile[ty + 8 * q][tx] = v[q];
+    }
+    __syncthreads();
+    const int k = k0 + tx;
+#pragma unroll
+    for (int q = 0; q < kDT / 8; ++q) {
+        const int pp = p0 + ty + 8 * q;
+        if (k < C && pp < P) {
+            const double2 w = tile[tx][ty + 8 * q];
+            const int64_t e = (int64_t)pp * C + k;
+            if (fp64)
+                static_cast<double2*>(vis)[e] = w;
+            else
+                static_cast<float2*>(vis)[e] = make_float2((float)w.x, (float)w.y);
+        }
     }
 }
 
@@ -158,7 +183,8 @@ cudaError_t launch_reduce_partials(const float2* partial, int n_split, int64_t C
 }
 
 cudaError_t launch_dump(double2* acc, int C, int P, void* vis, int fp64, cudaStream_t st) {
-    dump_kernel<<<grid_for((int64_t)C * P), 256, 0, st>>>(acc, C, P, vis, fp64);
+    dim3 grid((unsigned)((P + kDT - 1) / kDT), (unsigned)((C + kDT - 1) / kDT));
+    dump_kernel<<<grid, kDT * 8, 0, st>>>(acc, C, P, vis, fp64);
     return cudaGetLastError();
 }
 

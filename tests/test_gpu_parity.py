@@ -254,3 +254,21 @@ def test_tile_choices_keep_parity(lib, torch_cuda, window, stages, split):
         c.push(torch_cuda.from_numpy(packed.reshape(-1)).cuda(), S * K)
         V, n = c.dump(fp64=True)
     assert vis_error(V, R, N) <= TOL
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "fp32_simt", "fp16", "fp8"])
+@pytest.mark.parametrize("N,K,S", [(6, 2048, 70), (3, 4096, 37)])
+def test_large_k_every_workspace_type(lib, torch_cuda, dtype, N, K, S):
+    """K = 2048 and 4096 (the batching workload's long transforms) through
+    every workspace element type, with gains and fractional delays, over
+    several CTAs of frames and a ragged tail."""
+    packed, _ = synth.make_samples(N, S * K, K, seed=SEED + K + N)
+    g, tau = synth.gains_delays(N, seed=K)
+    g32 = np.asarray(g, np.complex64)
+    t32 = np.asarray(tau * 3.7, np.float32)
+    R, _ = oracle.correlate(packed, N, K, gains=g32.astype(np.complex128),
+                            delays=t32.astype(np.float64))
+    V, n = run_gpu(lib, torch_cuda, packed, N, K, dtype, gains=g32, delays=t32)
+    assert n == S
+    e = vis_error(V, R, N)
+    assert e <= PRECISION_BOUND.get(dtype, TOL), e

@@ -153,7 +153,6 @@ __global__ void __launch_bounds__(kThreads) fengine_generic(FengineArgs a, int F
 constexpr int kF512Frames = 32;     // frames per CTA (one 128-byte run per row)
 constexpr int kF512Threads = 256;   // 16 groups of 16 lanes, 2 frames per group
 constexpr int kXStride = 17;        // exchange row stride (complex), conflict-free
-constexpr int kStgStride = 33;      // staging row stride (floats), conflict-free
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -208,12 +207,14 @@ __device__ __forceinline__ void dft16(float2 (&x)[16]) {
 }
 
 // Nibble v (0..15, 4-bit two's complement) to float without a conversion
-// instruction: the bit pattern 0x4B000000 | u is the float 2^23 + u.
+// instruction: the bit pattern 0x4B000000 | u is the float 2^23 + u.  The
+// high nibble is masked in place (u = 16 (v ^ 8)) and scaled back by the
+// multiply-add, whose exact result needs no rounding.
 __device__ __forceinline__ float nib_lo(unsigned b) {
     return __int_as_float((int)((b & 15u) ^ 0x4B000008u)) - 8388616.0f;
 }
 __device__ __forceinline__ float nib_hi(unsigned b) {
-    return __int_as_float((int)(((b >> 4) & 15u) ^ 0x4B000008u)) - 8388616.0f;
+    return fmaf(__int_as_float((int)((b & 0xF0u) ^ 0x4B000080u)), 0.0625f, -524296.0f);
 }
 
 constexpr int kOutDebug = -1;

@@ -66,6 +66,8 @@ struct TcModeArgs {
     int n_split;
     int item_base, n_items;   // items: channel fastest, then block pair, then split
     int64_t S_pad, S_item;
+    int64_t tiles;            // k-tiles of the pass (balanced deal)
+    int64_t unit_base;        // first work unit of this mode (balanced deal)
     float2* partial;          // [n_split][C][P] FP32 partials (n_split > 1)
     double2* acc;             // [C][P] FP64 accumulator
     int* ticket;              // [C][npairs] arrival counters (n_split > 1), zero between launches
@@ -83,11 +85,39 @@ struct TcArgs {
     int* status;
     unsigned long long timeout_ns;
     int withhold;             // test hook: CTA 0 does not load its first k-tile
+    int balanced;             // 1: contiguous deal of weighted k-tiles; 0: round-robin items
+    int64_t units;            // total work units of the balanced deal
 };
 
 struct Item {
     int m, k, b1, b2, sp, pr;
 };
+
+// One CTA's share of an item: k-tiles [s_beg, s_end) of the pass, the
+// item's slot among the CTAs sharing it and their number.
+struct Piece {
+    Item itm;
+    int64_t s_beg, s_end;
+    int slot, nslots;
+};
+
+// Work units per k-tile: 2 for a diagonal block pair (one tile loaded, two
+// MMAs in FP32 mode), 3 for an off-diagonal one (two tiles, three MMAs).
+// Each item (with k-tiles) starts with kEndUnits more, standing for the cost
+// of an item's end (~4 k-tiles); they hold no k-tile.
+constexpr int kEndUnits = 8;
+
+__host__ __device__ __forceinline__ int64_t item_units(int64_t tiles, int w) {
+    return tiles > 0 ? kEndUnits + tiles * w : 0;
+}
+__device__ __forceinline__ int pair_units(int pr, int nblk) {
+    int b1 = 0;
+    while (pr >= nblk - b1) {
+        pr -= nblk - b1;
+        ++b1;
+    }
+    return pr == 0 ? 2 : 3;
+}
 
 __device__ __forceinline__ Item decode_item(const TcArgs& a, int g) {
     int m = 0;
@@ -112,6 +142,100 @@ __device__ __forceinline__ Item decode_item(const TcArgs& a, int g) {
 }
 
 __device__ __forceinline__ int block_ants(int N, int b) { return min(64, N - 64 * b); }
+
+// The pieces of one CTA, in the same order for every role.
+//
+// Balanced deal: every mode's items (block pair major, channel fastest) are
+// laid end to end as k-tiles of pair_units() units each, U units in all; CTA
+// c owns the k-tiles whose first unit u has floor(u G / U) = c, so every CTA
+// gets the same work to within one k-tile, whatever the channel count.  An
+// item cut between CTAs is combined by the last of them (ticket).
+// Round-robin deal (tile choices fixed by the caller): item g goes to CTA
+// g mod G, its range is split number sp of n_split equal ranges.
+struct PieceCursor {
+    int m, pr, k, g;
+    int64_t ibase, lo, hi;
+};
+
+__device__ __forceinline__ int64_t ceil_div64(int64_t x, int64_t y) { return (x + y - 1) / y; }
+
+__device__ __forceinline__ void cursor_init(const TcArgs& a, PieceCursor& c) {
+    c.g = blockIdx.x;
+    c.m = a.n_modes;
+    if (!a.balanced) return;
+    const int64_t G = gridDim.x;
+    c.lo = ceil_div64((int64_t)blockIdx.x * a.units, G);
+    c.hi = ceil_div64((int64_t)(blockIdx.x + 1) * a.units, G);
+    for (int m = 0; m < a.n_modes; ++m) {
+        const TcModeArgs& d = a.md[m];
+        int64_t base = d.unit_base;
+        for (int pr = 0; pr < d.npairs; ++pr) {
+            const int64_t iu = item_units(d.tiles, pair_units(pr, d.nblk));
+            const int64_t pu = iu * d.C;
+            if (c.lo < base + pu) {
+                c.m = m;
+                c.pr = pr;
+                c.k = (int)((c.lo - base) / iu);
+                c.ibase = base + (int64_t)c.k * iu;
+                return;
+            }
+            base += pu;
+        }
+    }
+}
+
+__device__ __forceinline__ bool next_piece(const TcArgs& a, PieceCursor& c, Piece& p) {
+    if (!a.balanced) {
+        if (c.g >= a.total_items) return false;
+        p.itm = decode_item(a, c.g);
+        const TcModeArgs& d = a.md[p.itm.m];
+        p.s_beg = (int64_t)p.itm.sp * d.S_item;
+        p.s_end = min(d.S_pad, p.s_beg + d.S_item);
+        p.slot = p.itm.sp;
+        p.nslots = d.n_split;
+        c.g += gridDim.x;
+        return true;
+    }
+    const int64_t G = gridDim.x;
+    while (c.m < a.n_modes && c.ibase < c.hi) {
+        const TcModeArgs& d = a.md[c.m];
+        const int w = pair_units(c.pr, d.nblk);
+        const int64_t t0 = c.ibase + kEndUnits;          // first unit of k-tile 0
+        const int64_t j0 = c.lo > t0 ? ceil_div64(c.lo - t0, w) : 0;
+        const int64_t j1 = c.hi > t0 ? min(d.tiles, ceil_div64(c.hi - t0, w)) : 0;
+        const bool mine = j0 < j1;
+        if (mine) {
+            int pr = c.pr, b1 = 0;
+            while (pr >= d.nblk - b1) {
+                pr -= d.nblk - b1;
+                ++b1;
+            }
+            p.itm.m = c.m;
+            p.itm.k = c.k;
+            p.itm.pr = c.pr;
+            p.itm.b1 = b1;
+            p.itm.b2 = b1 + pr;
+            p.itm.sp = 0;
+            const int64_t KT = a.KT;
+            p.s_beg = j0 * KT;
+            p.s_end = j1 * KT;
+            const int first = (int)(t0 * G / a.units);
+            const int last = (int)((t0 + (d.tiles - 1) * w) * G / a.units);
+            p.slot = (int)blockIdx.x - first;
+            p.nslots = last - first + 1;
+        }
+        c.ibase += item_units(d.tiles, w);
+        if (++c.k == d.C) {
+            c.k = 0;
+            if (++c.pr == d.npairs) {
+                c.pr = 0;
+                ++c.m;
+            }
+        }
+        if (mine) return true;
+    }
+    return false;
+}
 
 // ---------------------------------------------------------------- PTX helpers
 
@@ -261,6 +385,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_word = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* epi_last = abort_word + 2;
+    PieceCursor* epi_cur = reinterpret_cast<PieceCursor*>(
+        (reinterpret_cast<uintptr_t>(epi_last + 2) + 15) & ~(uintptr_t)15);
+    Piece* epi_pc = reinterpret_cast<Piece*>(epi_cur + 1);
+    volatile int* epi_more = reinterpret_cast<volatile int*>(epi_pc + 1);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -298,15 +426,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
             int armed_phase[16];
             for (int s = 0; s < 16; ++s) armed_phase[s] = -1;
             bool ok = true;
-            for (int g = blockIdx.x; ok && g < a.total_items; g += gridDim.x) {
-                const Item itm = decode_item(a, g);
+            PieceCursor cur;
+            cursor_init(a, cur);
+            Piece pc;
+            while (ok && next_piece(a, cur, pc)) {
+                const Item& itm = pc.itm;
                 const TcModeArgs& d = a.md[itm.m];
                 const CUtensorMap* map = &a.tmap[itm.m];
                 const bool diag = itm.b1 == itm.b2;
                 const int ra = kRows * itm.b1;
                 const int rb = kRows * itm.b2;
-                const int64_t s_beg = (int64_t)itm.sp * d.S_item;
-                const int64_t s_end = min(d.S_pad, s_beg + d.S_item);
+                const int64_t s_beg = pc.s_beg;
+                const int64_t s_end = pc.s_end;
                 for (int64_t s = s_beg; s < s_end; s += step, ++it) {
                     const uint32_t st = it % a.stages;
                     const uint32_t ph = (it / a.stages) & 1u;
@@ -352,8 +483,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
             int wi = 0;
             bool ok = true;
             bool issued = false;
-            for (int g = blockIdx.x; ok && g < a.total_items; g += gridDim.x) {
-                const Item itm = decode_item(a, g);
+            PieceCursor cur;
+            cursor_init(a, cur);
+            Piece pc;
+            while (ok && next_piece(a, cur, pc)) {
+                const Item& itm = pc.itm;
                 const TcModeArgs& d = a.md[itm.m];
                 const bool diag = itm.b1 == itm.b2;
                 const int Nn = (2 * block_ants(d.N, itm.b2) + 15) & ~15;
@@ -361,8 +495,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                 // N>>3 at bits 17-22, M>>4 at bits 24-28
                 const uint32_t idesc =
                     (1u << 4) | ((uint32_t)(Nn >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
-                const int64_t s_beg = (int64_t)itm.sp * d.S_item;
-                const int64_t s_end = min(d.S_pad, s_beg + d.S_item);
+                const int64_t s_beg = pc.s_beg;
+                const int64_t s_end = pc.s_end;
                 for (int64_t w0 = s_beg; ok && w0 < s_end; w0 += a.W, ++wi) {
                     const int b = wi & 1;
                     const uint32_t aph = (uint32_t)(wi >> 1) & 1u;
@@ -438,8 +572,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
         const int h = (warp - 2) >> 2;
         const int r = 32 * q + lane;
         int wi = 0;
-        for (int g = blockIdx.x; g < a.total_items; g += gridDim.x) {
-            const Item itm = decode_item(a, g);
+        // one cursor for the 8 warps, in shared memory (registers are scarce here)
+        if (et == 0) cursor_init(a, *epi_cur);
+        for (;;) {
+            if (et == 0) *epi_more = next_piece(a, *epi_cur, *epi_pc) ? 1 : 0;
+            epi_sync();
+            if (!*epi_more) break;
+            const Piece pc = *epi_pc;
+            const Item& itm = pc.itm;
             const TcModeArgs& d = a.md[itm.m];
             const bool diag = itm.b1 == itm.b2;
             const bool use_t = MODE == 0 && diag;
@@ -449,8 +589,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
             const int R2b = 2 * nb2;
             const int NH = ((R2b + 15) & ~15) >> 1;  // columns per half, multiple of 8
             const int col0 = h * NH;
-            const int64_t s_beg = (int64_t)itm.sp * d.S_item;
-            const int64_t s_end = min(d.S_pad, s_beg + d.S_item);
+            const int64_t s_beg = pc.s_beg;
+            const int64_t s_end = pc.s_end;
             float gacc[64], tacc[64];
 #pragma unroll
             for (int j = 0; j < 64; ++j) {
@@ -522,7 +662,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
             const float gs = MODE == 0 ? 1.0f / (kSplitScale * kSplitScale) : 1.0f;
             const int N = d.N, C = d.C, P = d.P;
             const int npl = diag ? nb1 * (nb1 + 1) / 2 : nb1 * nb2;
-            const bool direct = d.n_split == 1;
+            const bool direct = pc.nslots == 1;
             {
                 // kVB pairs per thread at a time: their accumulator loads are
                 // issued together, so their latencies overlap
@@ -575,20 +715,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
 #pragma unroll
                         for (int u = 0; u < kVB; ++u)
                             if (pp[u] >= 0)
-                                d.partial[((int64_t)itm.sp * C + itm.k) * P + pp[u]] =
+                                d.partial[((int64_t)pc.slot * C + itm.k) * P + pp[u]] =
                                     make_float2(vre[u], vim[u]);
                     }
                 }
             }
             if (!direct) {
-                // The last of the n_split items of this (channel, block pair) to
-                // finish adds every partial, in split order, into the FP64
+                // The last of the CTAs sharing this (channel, block pair) to
+                // finish adds every partial, in slot order, into the FP64
                 // accumulator: deterministic, and no reduction launch.
                 __threadfence();
                 epi_sync();
                 if (et == 0) {
                     const int old = atomicAdd(d.ticket + itm.k * d.npairs + itm.pr, 1);
-                    *epi_last = old == d.n_split - 1 ? 1 : 0;
+                    *epi_last = old == pc.nslots - 1 ? 1 : 0;
                 }
                 epi_sync();
                 if (*epi_last) {
@@ -611,7 +751,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                         const int j = 64 * itm.b2 + lj;
                         const int p = i * N - i * (i - 1) / 2 + (j - i);
                         double re = 0.0, im = 0.0;
-                        for (int sp = 0; sp < d.n_split; ++sp) {
+                        for (int sp = 0; sp < pc.nslots; ++sp) {
                             const float2 v = __ldcg(d.partial + ((int64_t)sp * C + itm.k) * P + p);
                             re += (double)v.x;
                             im += (double)v.y;
@@ -661,6 +801,14 @@ constexpr size_t kSmemBudget = 227 * 1024;
 
 }  // namespace
 
+// How a launch deals its work to the CTAs (see next_piece).
+struct DealPlan {
+    std::vector<int> sp;      // round-robin deal: ranges per item of each mode
+    bool balanced = false;    // contiguous deal of weighted k-tiles instead
+    int grid = 0;             // CTAs of the balanced deal
+    int64_t units = 0;        // its total work units
+};
+
 struct TcPlan {
     int N = 0, C = 0, P = 0, nblk = 1, npairs = 1;
     int mode = 0, planes = 1, KT = 64;
@@ -678,7 +826,7 @@ struct TcPlan {
     unsigned long long hook_timeout_ns = 0;
     int* ticket = nullptr;               // [C][npairs] arrival counters
     // split decisions already made, keyed by the S_pad of every mode in the launch
-    std::vector<std::pair<std::vector<int64_t>, std::vector<int>>> split_cache;
+    std::vector<std::pair<std::vector<int64_t>, DealPlan>> split_cache;
 };
 
 int tc_plan_create(TcPlan** out, int N, int C, int spec_type, std::string& err) {
@@ -777,6 +925,16 @@ int tc_set_tiles(TcPlan* p, int window, int stages, int split, int atoms, std::s
 
 namespace {
 
+// Work units per k-tile of block pair pr, as pair_units() on the device.
+int host_pair_units(int pr, int nblk) {
+    int b1 = 0;
+    while (pr >= nblk - b1) {
+        pr -= nblk - b1;
+        ++b1;
+    }
+    return pr == 0 ? 2 : 3;
+}
+
 struct LaunchShape {
     int two_tiles, gs_floats, stages, W, atoms;
     size_t smem;
@@ -790,7 +948,7 @@ LaunchShape launch_shape(TcPlan* const* plans, int n) {
         r2max = std::max(r2max, 2 * std::min(64, plans[m]->N));
     }
     L.gs_floats = r2max * (r2max + 1);
-    const size_t fixed = 1024 + (size_t)L.gs_floats * 4 + 16 + 16 + 8 * (2 * 16 + 5);
+    const size_t fixed = 1024 + (size_t)L.gs_floats * 4 + 16 + 16 + 8 * (2 * 16 + 5) + 256;
     auto fit = [&](int atoms) {
         const size_t sb = (size_t)plans[0]->planes * atoms * kTileBytes * (L.two_tiles ? 2 : 1);
         return std::min<int>(16, (int)((kSmemBudget - fixed) / sb));
@@ -820,20 +978,27 @@ LaunchShape launch_shape(TcPlan* const* plans, int n) {
     return L;
 }
 
-// Work-list split: every mode's pass of S_pad frames is cut into n_split
-// ranges of whole k-tiles.  The choice minimises the busiest CTA's work under
-// the kernel's round-robin deal, preferring one range per channel (the
-// epilogue then accumulates in FP64 directly and no reduction is launched).
-std::vector<int> choose_splits(TcPlan* const* plans, int n, const int64_t* S_pad) {
+// Work deal of one launch.  Round-robin: every mode's pass of S_pad frames
+// is cut into n_split ranges of whole k-tiles per item and items go to CTAs
+// in turn; the range count minimises the busiest CTA's work in a simulation
+// of that deal.  Balanced (single-mode launches): contiguous shares of the
+// weighted k-tiles (see next_piece).  The cheaper of the two in the same
+// cost model is taken (per item or piece: its k-tiles x 1 on a diagonal
+// block pair, x 1.5 off it, plus ~4 k-tiles for its end, measured on GB300,
+// and 2 more when its partial is combined with others).  At N = 44, K = 512
+// and 8192 frames per pass the round-robin deal leaves 104 CTAs with two
+// channels and 48 with one; the balanced deal gives each 1.7 channels.
+DealPlan choose_deal(TcPlan* const* plans, int n, const int64_t* S_pad) {
     std::vector<int64_t> key(S_pad, S_pad + n);
+    DealPlan out;
     if (plans[0]->split > 0) {
-        // fixed by corr_set_tiles: ranges per channel, at most one per k-tile
-        std::vector<int> fixed(n);
+        // fixed by corr_set_tiles: round-robin, ranges per channel, at most one per k-tile
+        out.sp.resize(n);
         for (int m = 0; m < n; ++m) {
             const int64_t tiles = std::max<int64_t>(1, S_pad[m] / plans[m]->KT);
-            fixed[m] = (int)std::min<int64_t>(std::min(plans[0]->split, plans[m]->max_split), tiles);
+            out.sp[m] = (int)std::min<int64_t>(std::min(plans[0]->split, plans[m]->max_split), tiles);
         }
-        return fixed;
+        return out;
     }
     auto& cache = plans[0]->split_cache;
     for (auto& e : cache)
@@ -846,14 +1011,12 @@ std::vector<int> choose_splits(TcPlan* const* plans, int n, const int64_t* S_pad
     std::vector<double> load(sms);
     for (int64_t T = 1; T <= max_tiles * 2; T *= 2) {
         std::vector<int> sp(n);
-        bool needs_reduce = false;
         for (int m = 0; m < n; ++m) {
             const int64_t tiles = std::max<int64_t>(1, S_pad[m] / plans[m]->KT);
             int64_t ns = (tiles + T - 1) / T;
             ns = std::min<int64_t>(ns, plans[m]->max_split);
             const int64_t per = (tiles + ns - 1) / ns;
             sp[m] = (int)((tiles + per - 1) / per);
-            needs_reduce |= sp[m] > 1;
         }
         std::fill(load.begin(), load.end(), 0.0);
         int64_t g = 0;
@@ -864,23 +1027,70 @@ std::vector<int> choose_splits(TcPlan* const* plans, int n, const int64_t* S_pad
             for (int s = 0; s < sp[m]; ++s) {
                 const int64_t t = std::min<int64_t>(per, tiles - (int64_t)s * per);
                 for (int pr = 0; pr < p->npairs; ++pr) {
-                    // cost in k-tiles: the tiles, plus the end of an item (~4 k-tiles
-                    // measured on GB300) and the in-kernel combine of split partials
-                    const double w = (double)t * (p->nblk > 1 ? 1.5 : 1.0) + 4.0 + (sp[m] > 1 ? 2.0 : 0.0);
+                    const double w = (double)t * 0.5 * host_pair_units(pr, p->nblk) + 4.0 +
+                                     (sp[m] > 1 ? 2.0 : 0.0);
                     for (int k = 0; k < p->C; ++k, ++g) load[g % sms] += w;
                 }
             }
         }
-        double score = *std::max_element(load.begin(), load.end());
-        (void)needs_reduce;
+        const double score = *std::max_element(load.begin(), load.end());
         if (score < best_score - 1e-9) {
             best_score = score;
             best = sp;
         }
     }
-    cache.emplace_back(key, best);
+    out.sp = best;
+    // balanced deal: every CTA gets U/G units; an item then spans at most
+    // (tiles - 1) w G / U + 2 CTAs, which must fit the partial slots, and a
+    // CTA holds at least 3 units (the heaviest k-tile), so it owns a k-tile of
+    // every item it overlaps and an item's CTAs are consecutive
+    int64_t units = 0, max_span = 0;
+    int cap_slots = 1 << 30;
+    for (int m = 0; m < n; ++m) {
+        const TcPlan* p = plans[m];
+        const int64_t tiles = S_pad[m] / p->KT;
+        for (int pr = 0; pr < p->npairs; ++pr) {
+            const int w = host_pair_units(pr, p->nblk);
+            units += item_units(tiles, w) * p->C;
+            if (tiles > 0) max_span = std::max<int64_t>(max_span, (tiles - 1) * w);
+        }
+        cap_slots = std::min(cap_slots, p->max_split);
+    }
+    // (one mode only: with several, the round-robin deal spreads every mode's
+    // items, whose ends differ in cost, evenly over the CTAs -- measured
+    // faster on the four-mode batch)
+    if (n == 1 && units > 0 && cap_slots >= 3) {
+        int64_t G = sms;
+        if (max_span > 0)
+            G = std::min<int64_t>(G, std::max<int64_t>(1, (int64_t)(cap_slots - 2) * units / max_span));
+        G = std::min<int64_t>(G, std::max<int64_t>(1, units / 3));
+        std::vector<double> bl(G, 0.0);
+        int64_t ibase = 0;
+        for (int m = 0; m < n; ++m) {
+            const TcPlan* p = plans[m];
+            const int64_t tiles = S_pad[m] / p->KT;
+            if (tiles == 0) continue;
+            for (int pr = 0; pr < p->npairs; ++pr) {
+                const int w = host_pair_units(pr, p->nblk);
+                for (int k = 0; k < p->C; ++k, ibase += item_units(tiles, w)) {
+                    const int64_t t0 = ibase + kEndUnits;
+                    const int64_t first = t0 * G / units;
+                    const int64_t last = (t0 + (tiles - 1) * w) * G / units;
+                    for (int64_t j = 0; j < tiles; ++j) bl[(t0 + j * w) * G / units] += 0.5 * w;
+                    for (int64_t c = first; c <= last; ++c) bl[c] += 4.0 + (last > first ? 2.0 : 0.0);
+                }
+            }
+        }
+        const double score = *std::max_element(bl.begin(), bl.end());
+        if (score < best_score - 1e-9) {
+            out.balanced = true;
+            out.grid = (int)G;
+            out.units = units;
+        }
+    }
+    cache.emplace_back(key, out);
     if (cache.size() > 16) cache.erase(cache.begin());
-    return best;
+    return out;
 }
 
 }  // namespace
@@ -902,7 +1112,8 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
     }
     std::vector<int64_t> S(n);
     for (int m = 0; m < n; ++m) S[m] = runs[m].S_pad;
-    const std::vector<int> sp = choose_splits(plans, n, S.data());
+    const DealPlan deal = choose_deal(plans, n, S.data());
+    const std::vector<int>& sp = deal.sp;
     const LaunchShape L = launch_shape(plans, n);
     TcArgs a;
     memset(&a, 0, sizeof a);
@@ -921,6 +1132,7 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
         plans[0]->withhold = 0;
     }
     int base = 0;
+    int64_t units = 0;
     for (int m = 0; m < n; ++m) {
         const TcPlan* p = plans[m];
         a.tmap[m] = p->tmap;
@@ -942,12 +1154,21 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
         d.acc = runs[m].acc;
         d.ticket = plans[m]->ticket;
         d.scale = runs[m].scale;
+        d.tiles = d.S_pad / p->KT;
+        d.unit_base = units;
+        for (int pr = 0; pr < p->npairs; ++pr)
+            units += item_units(d.tiles, host_pair_units(pr, p->nblk)) * p->C;
         runs[m].n_split = d.n_split;
         runs[m].direct = true;          // splits are combined inside the kernel
     }
     a.total_items = base;
     if (base == 0) return CORR_OK;
-    const int grid = std::min(base, plans[0]->num_sms);
+    int grid = std::min(base, plans[0]->num_sms);
+    if (deal.balanced) {
+        a.balanced = 1;
+        a.units = units;
+        grid = deal.grid;
+    }
     cudaError_t e;
     if (plans[0]->mode == 0) {
         e = cudaFuncSetAttribute(xengine_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -55,7 +55,6 @@ namespace {
 constexpr int kTcThreads = 320;     // producer, MMA, 8 epilogue warps
 constexpr int kRows = 128;          // MMA M = TMA box rows = one antenna block
 constexpr int kRowBytes = 128;      // one swizzle span per row
-constexpr int kTileBytes = kRows * kRowBytes;
 constexpr uint32_t kTmemCols = 512; // two accumulator sets of 256 columns
 constexpr int kStatusTimeout = 2;
 constexpr int kVB = 2;              // accumulator loads in flight per epilogue thread
@@ -67,6 +66,7 @@ struct TcModeArgs {
     int item_base, n_items;   // items: channel fastest, then block pair, then split
     int64_t S_pad, S_item;
     int64_t tiles;            // k-tiles of the pass (balanced deal)
+    uint32_t box_bytes;       // bytes one TMA box of this mode lands in shared memory
     int64_t unit_base;        // first work unit of this mode (balanced deal)
     float2* partial;          // [n_split][C][P] FP32 partials (n_split > 1)
     double2* acc;             // [C][P] FP64 accumulator
@@ -79,9 +79,11 @@ struct TcArgs {
     TcModeArgs md[kMaxTcModes];
     int n_modes, total_items;
     int stages, KT, W;
+    int kt_shift;             // log2(KT): the single-lane roles avoid 64-bit division
     int atoms;                // k-tiles of KT spectra per pipeline stage
     int two_tiles;            // stage slots hold separate A and B tiles
     int gs_floats;            // epilogue G buffer (largest 2nb x (2nb + 1) of the modes)
+    int slot_rows;            // rows of one operand tile slot in shared memory (<= 128)
     int* status;
     unsigned long long timeout_ns;
     int withhold;             // test hook: CTA 0 does not load its first k-tile
@@ -278,6 +280,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 // another role has already given up (the shared abort word is set).
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_word,
                                          const TcArgs& a) {
+    if (mbar_try_wait(bar, parity)) return true;
     unsigned long long t0 = 0;
     for (uint32_t n = 0;; ++n) {
         if (mbar_try_wait(bar, parity)) return true;
@@ -369,9 +372,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     constexpr int planes = MODE == 0 ? 2 : 1;
     // stage layout: [operand A|B][plane][atom] tiles of 16 KB
-    const uint32_t tile_set = planes * a.atoms * kTileBytes;    // one operand, all planes
-    const uint32_t stage_bytes = tile_set * (a.two_tiles ? 2u : 1u);
-    const uint32_t plane_off = (uint32_t)a.atoms * kTileBytes;   // hi -> lo plane
+    // Stage layout: per k-tile ("atom") [operand A | operand B][plane hi | lo],
+    // each a slot of slot_rows rows (2N rounded up to 8 for one antenna block,
+    // else 128).  The MMA reads 128 rows (and a diagonal pair's concatenated B
+    // operand 2 slot_rows rows) from a slot; rows past the antennas only feed
+    // outputs the epilogue ignores, and the ring is followed by enough shared
+    // memory for the reads past its last slot.
+    const uint32_t slot = (uint32_t)a.slot_rows * kRowBytes;
+    const uint32_t plane_off = slot;                                // hi -> lo plane
+    const uint32_t tile_set = planes * slot;                        // operand A -> B
+    const uint32_t atom_bytes = tile_set * (a.two_tiles ? 2u : 1u);
+    const uint32_t stage_bytes = atom_bytes * (uint32_t)a.atoms;
     const int step = a.KT * a.atoms;                             // spectra per stage
     unsigned char* stages = smem;
     float* Gs = reinterpret_cast<float*>(smem + a.stages * stage_bytes);   // <= 128 x 129
@@ -422,9 +433,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
     if (warp == 0) {
         // ------------------------------------------------------ TMA producer
         if (lane == 0) {
-            uint32_t it = 0;
-            int armed_phase[16];
-            for (int s = 0; s < 16; ++s) armed_phase[s] = -1;
+            uint32_t it = 0, st = 0, ph = 0;       // stage slot and its phase parity
+            uint32_t armed = 0, armed_ph = 0;     // slots with copies in flight, their parity
             bool ok = true;
             PieceCursor cur;
             cursor_init(a, cur);
@@ -439,22 +449,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                 const int64_t s_beg = pc.s_beg;
                 const int64_t s_end = pc.s_end;
                 for (int64_t s = s_beg; s < s_end; s += step, ++it) {
-                    const uint32_t st = it % a.stages;
-                    const uint32_t ph = (it / a.stages) & 1u;
+                    if (it > 0 && ++st == (uint32_t)a.stages) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
                     if (!wait_bar(smem_u32(&empty[st]), ph ^ 1u, abort_word, a)) {
                         ok = false;
                         break;
                     }
                     if (a.withhold && blockIdx.x == 0 && it == 0) continue;   // test hook
-                    const int n_at = (int)min((int64_t)a.atoms, (s_end - s) / a.KT);
+                    const int n_at = (int)min((int64_t)a.atoms, (s_end - s) >> a.kt_shift);
                     const uint32_t bytes =
-                        (uint32_t)n_at * planes * kTileBytes * (diag ? 1u : 2u);
+                        (uint32_t)n_at * planes * d.box_bytes * (diag ? 1u : 2u);
                     const uint32_t fb = smem_u32(&full[st]);
                     mbar_expect_tx(fb, bytes);
                     const uint32_t dst = smem_u32(stages + st * stage_bytes);
                     for (int at = 0; at < n_at; ++at) {
                         const int sa = (int)s + at * a.KT;
-                        const uint32_t o = (uint32_t)at * kTileBytes;
+                        const uint32_t o = (uint32_t)at * atom_bytes;
                         tma_load_3d(dst + o, map, fb, sa, ra, itm.k);
                         if (planes == 2) tma_load_3d(dst + plane_off + o, map, fb, sa, ra, d.C + itm.k);
                         if (!diag) {
@@ -463,15 +475,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                                 tma_load_3d(dst + tile_set + plane_off + o, map, fb, sa, rb, d.C + itm.k);
                         }
                     }
-                    armed_phase[st] = (int)ph;
+                    armed |= 1u << st;
+                    armed_ph = (armed_ph & ~(1u << st)) | (ph << st);
                 }
             }
             if (!ok) {
                 // drain: every armed stage's copies must land before teardown
                 const unsigned long long d2 = globaltimer() + a.timeout_ns;
-                for (int s = 0; s < a.stages && s < 16; ++s) {
-                    if (armed_phase[s] < 0) continue;
-                    while (!mbar_try_wait(smem_u32(&full[s]), (uint32_t)armed_phase[s]))
+                for (int s2 = 0; s2 < a.stages && s2 < 16; ++s2) {
+                    if (!((armed >> s2) & 1u)) continue;
+                    while (!mbar_try_wait(smem_u32(&full[s2]), (armed_ph >> s2) & 1u))
                         if (globaltimer() > d2) break;
                 }
             }
@@ -479,7 +492,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
     } else if (warp == 1) {
         // ------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            uint32_t it = 0;
+            uint32_t it = 0, st = 0, ph = 0;
             int wi = 0;
             bool ok = true;
             bool issued = false;
@@ -495,6 +508,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                 // N>>3 at bits 17-22, M>>4 at bits 24-28
                 const uint32_t idesc =
                     (1u << 4) | ((uint32_t)(Nn >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+                // FP32 mode, diagonal pair: B = [hi; lo] rows of the same tile pair,
+                // N = 2 slot_rows, so one MMA forms [Dhh | Dhl] (Dhl from column slot_rows)
+                const uint32_t idesc_cat = (1u << 4) | ((uint32_t)((2 * a.slot_rows) >> 3) << 17) |
+                                           ((uint32_t)(kRows >> 4) << 24);
                 const int64_t s_beg = pc.s_beg;
                 const int64_t s_end = pc.s_end;
                 for (int64_t w0 = s_beg; ok && w0 < s_end; w0 += a.W, ++wi) {
@@ -506,29 +523,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                     }
                     tc_fence_after();
                     const uint32_t d0 = tmem + (uint32_t)b * 256u;
-                    const uint32_t d1 = d0 + 128u;
                     const int64_t w1 = min(s_end, w0 + a.W);
                     uint32_t acc = 0;
                     for (int64_t s = w0; s < w1; s += step, ++it) {
-                        const uint32_t st = it % a.stages;
-                        const uint32_t ph = (it / a.stages) & 1u;
+                        if (it > 0 && ++st == (uint32_t)a.stages) {
+                            st = 0;
+                            ph ^= 1u;
+                        }
                         if (!wait_bar(smem_u32(&full[st]), ph, abort_word, a)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
                         const uint32_t base = smem_u32(stages + st * stage_bytes);
-                        const int n_at = (int)min((int64_t)a.atoms, (w1 - s) / a.KT);
+                        const int n_at = (int)min((int64_t)a.atoms, (w1 - s) >> a.kt_shift);
                         for (int at = 0; at < n_at; ++at) {
-                            const uint32_t ab = base + (uint32_t)at * kTileBytes;
+                            const uint32_t ab = base + (uint32_t)at * atom_bytes;
 #pragma unroll
                             for (int kk = 0; kk < 4; ++kk) {
                                 const uint64_t ah = sw128_desc(ab + 32u * kk);
                                 if (MODE == 0) {
                                     const uint64_t al = sw128_desc(ab + plane_off + 32u * kk);
                                     if (diag) {
-                                        mma<MODE>(d0, ah, ah, idesc, acc);
-                                        mma<MODE>(d1, ah, al, idesc, acc);
+                                        mma<MODE>(d0, ah, ah, idesc_cat, acc);
                                     } else {
                                         const uint64_t bh = sw128_desc(ab + tile_set + 32u * kk);
                                         const uint64_t bl = sw128_desc(ab + tile_set + plane_off + 32u * kk);
@@ -619,7 +636,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                         tmem_ld8(trow + 8u * c, v);
                         if (use_t) {
                             uint32_t w[8];
-                            tmem_ld8(trow + 128u + 8u * c, w);
+                            tmem_ld8(trow + (uint32_t)a.slot_rows + 8u * c, w);
                             tmem_ld_wait();
 #pragma unroll
                             for (int j = 0; j < 8; ++j) {
@@ -813,6 +830,7 @@ struct TcPlan {
     int N = 0, C = 0, P = 0, nblk = 1, npairs = 1;
     int mode = 0, planes = 1, KT = 64;
     int num_sms = 0;
+    int box_rows = 128;       // TMA box rows: 2N rounded up to 8 for one block, else 128
     CUtensorMap tmap;
     bool have_map = false;
     int64_t cap = 0;
@@ -844,6 +862,7 @@ int tc_plan_create(TcPlan** out, int N, int C, int spec_type, std::string& err) 
     p->mode = spec_type == SPEC_F16X2 ? 0 : (spec_type == SPEC_F16 ? 1 : 2);
     p->planes = p->mode == 0 ? 2 : 1;
     p->KT = p->mode == 2 ? 128 : 64;
+    p->box_rows = p->nblk == 1 ? (2 * N + 7) / 8 * 8 : kRows;
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -878,7 +897,7 @@ int tc_plan_update(TcPlan* p, void* spec, int64_t cap, int N, int C, int spec_ty
     const int R2 = 2 * p->N;
     cuuint64_t dims[3] = {(cuuint64_t)cap, (cuuint64_t)R2, (cuuint64_t)p->planes * p->C};
     cuuint64_t strides[2] = {(cuuint64_t)cap * eb, (cuuint64_t)R2 * cap * eb};
-    cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / eb), (cuuint32_t)kRows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / eb), (cuuint32_t)p->box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt =
         eb == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
@@ -936,7 +955,7 @@ int host_pair_units(int pr, int nblk) {
 }
 
 struct LaunchShape {
-    int two_tiles, gs_floats, stages, W, atoms;
+    int two_tiles, gs_floats, stages, W, atoms, slot_rows;
     size_t smem;
 };
 
@@ -948,9 +967,14 @@ LaunchShape launch_shape(TcPlan* const* plans, int n) {
         r2max = std::max(r2max, 2 * std::min(64, plans[m]->N));
     }
     L.gs_floats = r2max * (r2max + 1);
-    const size_t fixed = 1024 + (size_t)L.gs_floats * 4 + 16 + 16 + 8 * (2 * 16 + 5) + 256;
+    L.slot_rows = 8;
+    for (int m = 0; m < n; ++m) L.slot_rows = std::max(L.slot_rows, plans[m]->box_rows);
+    const size_t slot = (size_t)L.slot_rows * kRowBytes;
+    // + the rows an MMA reads past the ring's last slot
+    const size_t fixed = 1024 + (size_t)L.gs_floats * 4 + 16 + 16 + 8 * (2 * 16 + 5) + 256 +
+                         (size_t)(kRows - L.slot_rows) * kRowBytes;
     auto fit = [&](int atoms) {
-        const size_t sb = (size_t)plans[0]->planes * atoms * kTileBytes * (L.two_tiles ? 2 : 1);
+        const size_t sb = (size_t)plans[0]->planes * atoms * slot * (L.two_tiles ? 2 : 1);
         return std::min<int>(16, (int)((kSmemBudget - fixed) / sb));
     };
     // k-tiles per stage: as many (up to 4) as still leave 3 stages, unless set
@@ -965,7 +989,7 @@ LaunchShape launch_shape(TcPlan* const* plans, int n) {
     }
     while (L.atoms > 1 && fit(L.atoms) < 2) L.atoms /= 2;
     const size_t stage_bytes =
-        (size_t)plans[0]->planes * L.atoms * kTileBytes * (L.two_tiles ? 2 : 1);
+        (size_t)plans[0]->planes * L.atoms * slot * (L.two_tiles ? 2 : 1);
     const int smax = fit(L.atoms);
     L.stages = plans[0]->stages ? std::min(plans[0]->stages, smax) : std::min(smax, 8);
     const int step = plans[0]->KT * L.atoms;
@@ -1120,10 +1144,12 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
     a.n_modes = n;
     a.stages = L.stages;
     a.KT = plans[0]->KT;
+    a.kt_shift = a.KT == 128 ? 7 : 6;
     a.W = L.W;
     a.atoms = L.atoms;
     a.two_tiles = L.two_tiles;
     a.gs_floats = L.gs_floats;
+    a.slot_rows = L.slot_rows;
     a.status = runs[0].status;
     a.timeout_ns = plans[0]->timeout_ns;
     if (plans[0]->withhold) {
@@ -1155,6 +1181,7 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
         d.ticket = plans[m]->ticket;
         d.scale = runs[m].scale;
         d.tiles = d.S_pad / p->KT;
+        d.box_bytes = (uint32_t)p->box_rows * kRowBytes;
         d.unit_base = units;
         for (int pr = 0; pr < p->npairs; ++pr)
             units += item_units(d.tiles, host_pair_units(pr, p->nblk)) * p->C;

@@ -362,29 +362,34 @@ def main():
     if args.e2e_steps > 0:
         host_in = torch.empty(dev_in.numel(), dtype=torch.uint8, pin_memory=True)
         host_in.copy_(dev_in)
-        host_vis = np.empty((P, C), np.complex64)
+        host_vis = torch.empty((P, C), dtype=torch.complex64, pin_memory=True)
         hb = host_in.data_ptr()
 
         def step_host():
+            # pushes from pinned host memory, then the integration's
+            # visibilities queued into pinned host memory: the next step's
+            # copies start while this one is reduced and read back
             for f0, nf in pushes:
                 corr.corr_push(h, hb + f0 * rec, nf * K_FFT)
-            return corr.corr_dump(h, host_vis)
+            return corr.corr_dump_async(h, host_vis)
 
         step_host()
-        torch.cuda.synchronize()
+        corr.corr_sync(h)
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             step_host()
+        corr.corr_sync(h)                   # the last step's visibilities are in host memory
         te = time.perf_counter() - t0
         if dist:
             tt = torch.tensor([te], device="cuda", dtype=torch.float64)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             te = float(tt.item())
         e2e = {"value": world * N_ANT * frames * K_FFT * args.e2e_steps / te, "unit": UNIT,
-               "h2d_bytes_per_step": frames * rec, "d2h_bytes_per_step": host_vis.nbytes,
-               "steps": args.e2e_steps}
+               "h2d_bytes_per_step": frames * rec,
+               "d2h_bytes_per_step": host_vis.numel() * host_vis.element_size(),
+               "steps": args.e2e_steps, "dump": "corr_dump_async into pinned host memory"}
         del host_in
 
     # TC vs FP32: the other X-engine precisions on the same integration

@@ -151,6 +151,15 @@ int corr_push(corr_t h, const uint8_t* samples, int64_t n);
  * Accumulation across pushes is in FP64 on the device. */
 int corr_dump(corr_t h, void* vis, int64_t* n_spec, int vis_fp64);
 
+/* As corr_dump, but queued on the handle's stream without waiting for it
+ * (no counterpart in the paper: it lets a streaming caller start pushing the
+ * next integration while this one is still being reduced and copied out).
+ * `vis` must be device memory or page-locked host memory (CORR_EINVAL
+ * otherwise); it is complete once corr_sync (or a later corr_dump) returns,
+ * and must not be read or reused before that.  *n_spec is set at once.  A
+ * device-side error of the queued work is reported by that later call. */
+int corr_dump_async(corr_t h, void* vis, int64_t* n_spec, int vis_fp64);
+
 /* Wait for the handle's queued work; reports device-side errors. */
 int corr_sync(corr_t h);
 

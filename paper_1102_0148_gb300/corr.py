@@ -45,6 +45,7 @@ _SIGS = {
     "corr_set_corrections": (_int, [_vp, _vp, _vp]),
     "corr_push": (_int, [_vp, _vp, _i64]),
     "corr_dump": (_int, [_vp, _vp, ctypes.POINTER(_i64), _int]),
+    "corr_dump_async": (_int, [_vp, _vp, ctypes.POINTER(_i64), _int]),
     "corr_sync": (_int, [_vp]),
     "corr_destroy": (None, [_vp]),
     "corr_last_error": (ctypes.c_char_p, [_vp]),
@@ -176,6 +177,14 @@ def corr_push(h, samples, n):
 def corr_dump(h, vis, fp64=False):
     n = _i64(0)
     _check(_lib.corr_dump(h, _addr(vis), ctypes.byref(n), 1 if fp64 else 0), h)
+    return n.value
+
+
+def corr_dump_async(h, vis, fp64=False):
+    """Queue the dump into device or page-locked host memory; `vis` is
+    complete after the next corr_sync.  Returns the spectra summed."""
+    n = _i64(0)
+    _check(_lib.corr_dump_async(h, _addr(vis), ctypes.byref(n), 1 if fp64 else 0), h)
     return n.value
 
 

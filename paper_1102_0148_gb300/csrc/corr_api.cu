@@ -23,6 +23,7 @@ constexpr int64_t kDefaultChunk = 8192;
 constexpr int64_t kMinDefaultChunk = 2048;
 constexpr size_t kDefaultWorkspaceBytes = (size_t)2 << 30;
 constexpr int64_t kSimtSplit = 256;   // frames per SIMT X-engine split
+constexpr int kHostStages = 4;         // device staging buffers for host input
 
 thread_local std::string g_create_error = "no error";
 
@@ -53,9 +54,12 @@ struct corr_s {
     float2* partial = nullptr;   // [max_split][C][P]
     int max_split = 0;
     int* status = nullptr;       // device-side error word
-    uint8_t* stage[2] = {nullptr, nullptr};
-    cudaEvent_t stage_free[2] = {nullptr, nullptr};
-    cudaEvent_t stage_full[2] = {nullptr, nullptr};
+    // host-input staging ring: copies run ahead of the F-engine by up to
+    // kHostStages - 1 chunks of stage_frames frames
+    uint8_t* stage[kHostStages] = {};
+    cudaEvent_t stage_free[kHostStages] = {};
+    cudaEvent_t stage_full[kHostStages] = {};
+    int64_t stage_frames = 0;
     int stage_next = 0;
     void* vis_dev = nullptr;
     int64_t n_spec = 0;
@@ -341,8 +345,11 @@ int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, doubl
     const int64_t rec = (int64_t)h->N * (h->K / 2);
     const bool host = !is_device_ptr(samples);
     if (host && !h->stage[0]) {
-        for (int b = 0; b < 2; ++b) {
-            CUDA_TRY(h, cudaMalloc((void**)&h->stage[b], (size_t)(h->cap * rec)));
+        // half a workspace pass per buffer (whole 128-frame blocks), so a
+        // pass's copies can run while the X-engine works on the previous one
+        h->stage_frames = std::max<int64_t>(kSpecPad, h->cap / 2 / kSpecPad * kSpecPad);
+        for (int b = 0; b < kHostStages; ++b) {
+            CUDA_TRY(h, cudaMalloc((void**)&h->stage[b], (size_t)(h->stage_frames * rec)));
             CUDA_TRY(h, cudaEventCreateWithFlags(&h->stage_free[b], cudaEventDisableTiming));
             CUDA_TRY(h, cudaEventCreateWithFlags(&h->stage_full[b], cudaEventDisableTiming));
         }
@@ -353,12 +360,13 @@ int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, doubl
             if (rc != CORR_OK) return rc;
         }
         const int64_t room = h->cap - h->fill;
-        const int64_t S = frames - f0 < room ? frames - f0 : room;
+        int64_t S = frames - f0 < room ? frames - f0 : room;
+        if (host && S > h->stage_frames) S = h->stage_frames;
         const uint8_t* din = samples + f0 * rec;
         int b = 0;
         if (host) {
             b = h->stage_next;
-            h->stage_next ^= 1;
+            h->stage_next = (b + 1) % kHostStages;
             CUDA_TRY(h, cudaStreamWaitEvent(h->copy_stream, h->stage_free[b], 0));
             CUDA_TRY(h, cudaMemcpyAsync(h->stage[b], din, (size_t)(S * rec), cudaMemcpyHostToDevice,
                                         h->copy_stream));
@@ -389,7 +397,7 @@ void destroy_impl(corr_t h) {
     cudaFree(h->grad_buf);
     cudaFree(h->status);
     cudaFree(h->vis_dev);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kHostStages; ++b) {
         cudaFree(h->stage[b]);
         if (h->stage_free[b]) cudaEventDestroy(h->stage_free[b]);
         if (h->stage_full[b]) cudaEventDestroy(h->stage_full[b]);
@@ -676,13 +684,13 @@ int corr_grad(corr_t h, const uint8_t* samples, int64_t n, const float* gains,
     return check_status(h);
 }
 
-int corr_dump(corr_t h, void* vis, int64_t* n_spec, int vis_fp64) {
-    if (!h) return CORR_EINVAL;
-    if (!vis) return set_err(h, CORR_EINVAL, "vis is NULL");
+namespace {
+
+// Queue the dump of the integration into `vis` on the handle's stream.
+int enqueue_dump(corr_t h, void* vis, int vis_fp64, bool dev) {
     int frc = flush(h);
     if (frc != CORR_OK) return frc;
     const size_t bytes = (size_t)h->C * h->P * (vis_fp64 ? sizeof(double2) : sizeof(float2));
-    const bool dev = is_device_ptr(vis);
     void* out = vis;
     if (!dev) {
         if (!h->vis_dev) CUDA_TRY(h, cudaMalloc(&h->vis_dev, (size_t)h->C * h->P * sizeof(double2)));
@@ -698,11 +706,39 @@ int corr_dump(corr_t h, void* vis, int64_t* n_spec, int vis_fp64) {
     CUDA_TRY(h, launch_dump(h->acc, h->C, h->P, out, vis_fp64, h->stream));
     prof_end(h, CORR_KERNEL_DUMP);
     if (!dev) CUDA_TRY(h, cudaMemcpyAsync(vis, out, bytes, cudaMemcpyDeviceToHost, h->stream));
+    return CORR_OK;
+}
+
+}  // namespace
+
+int corr_dump(corr_t h, void* vis, int64_t* n_spec, int vis_fp64) {
+    if (!h) return CORR_EINVAL;
+    if (!vis) return set_err(h, CORR_EINVAL, "vis is NULL");
+    int rc = enqueue_dump(h, vis, vis_fp64, is_device_ptr(vis));
+    if (rc != CORR_OK) return rc;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    int rc = check_status(h);
+    rc = check_status(h);
     if (n_spec) *n_spec = h->n_spec;
     h->n_spec = 0;
     return rc;
+}
+
+int corr_dump_async(corr_t h, void* vis, int64_t* n_spec, int vis_fp64) {
+    if (!h) return CORR_EINVAL;
+    if (!vis) return set_err(h, CORR_EINVAL, "vis is NULL");
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, vis) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(h, CORR_EINVAL, "corr_dump_async needs device or page-locked host memory");
+    }
+    const bool dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (!dev && at.type != cudaMemoryTypeHost)
+        return set_err(h, CORR_EINVAL, "corr_dump_async needs device or page-locked host memory");
+    int rc = enqueue_dump(h, vis, vis_fp64, dev);
+    if (rc != CORR_OK) return rc;
+    if (n_spec) *n_spec = h->n_spec;
+    h->n_spec = 0;
+    return CORR_OK;
 }
 
 int corr_sync(corr_t h) {

@@ -272,3 +272,47 @@ def test_large_k_every_workspace_type(lib, torch_cuda, dtype, N, K, S):
     assert n == S
     e = vis_error(V, R, N)
     assert e <= PRECISION_BOUND.get(dtype, TOL), e
+
+
+def test_host_pushes_across_chunk_changes(lib, torch_cuda):
+    """Host input goes through a ring of device staging buffers; a larger
+    workspace pass set between integrations must not outgrow them."""
+    N, K = 6, 256
+    packed, _ = synth.make_samples(N, 1500 * K, K, seed=SEED + 31)
+    R, _ = oracle.correlate(packed, N, K)
+    host = torch_cuda.from_numpy(packed.reshape(-1)).pin_memory()
+    with lib.Correlator(N, K, "fp32", chunk=256) as c:
+        c.push(host, 1500 * K)                  # 1500 frames through 128-frame staging slices
+        V1, n1 = c.dump(fp64=True)
+        lib.corr_set_chunk(c.h, 1024)
+        c.push(host, 1500 * K)
+        V2, n2 = c.dump(fp64=True)
+    assert n1 == n2 == 1500
+    assert vis_error(V1, R, N) <= TOL and vis_error(V2, R, N) <= TOL
+
+
+def test_dump_async_matches_dump(lib, torch_cuda):
+    """corr_dump_async queues the same result into page-locked host (or
+    device) memory; pageable host memory is refused."""
+    torch = torch_cuda
+    N, K, S = 8, 512, 300
+    packed, _ = synth.make_samples(N, 2 * S * K, K, seed=SEED + 41)
+    dev = torch.from_numpy(packed.reshape(-1)).cuda()
+    rec = N * K // 2
+    with lib.Correlator(N, K, "fp32") as c:
+        c.push(dev[: S * rec], S * K)
+        V_sync, n0 = c.dump()
+        pinned = torch.empty((c.P, c.C), dtype=torch.complex64).pin_memory()
+        on_dev = torch.empty((c.P, c.C), dtype=torch.complex64, device="cuda")
+        c.push(dev[: S * rec], S * K)
+        n1 = lib.corr_dump_async(c.h, pinned)
+        c.push(dev[S * rec:], S * K)            # the next integration, queued behind it
+        n2 = lib.corr_dump_async(c.h, on_dev)
+        lib.corr_sync(c.h)
+        with pytest.raises(lib.CorrError) as ei:
+            lib.corr_dump_async(c.h, np.empty((c.P, c.C), np.complex64))
+        assert ei.value.code == lib.CORR_EINVAL
+    assert n0 == n1 == n2 == S
+    assert np.array_equal(pinned.numpy(), V_sync)
+    R2, _ = oracle.correlate(packed[S:], N, K)
+    assert vis_error(on_dev.cpu().numpy(), R2, N) <= TOL

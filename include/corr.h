@@ -139,6 +139,18 @@ int corr_set_corrections(corr_t h, const float* gains, const float* delays);
 int corr_set_scales(corr_t h, const float* scales);
 int corr_get_scales(corr_t h, float* scales);
 
+/* Coarse delay tracking (the streaming form's integer sample shift; the
+ * paper only mentions a phase correction before accumulation, Sec. 2.1):
+ * every later push correlates y_i[t] = x_i[t - delays[i]] instead of x_i,
+ * t counting the samples of the stream pushed into this handle.  delays: N
+ * int32 in [0, K] (host or device), NULL or all zero = off.  The samples
+ * before a push come from the end of the previous one (the stream's history,
+ * carried on the device and in corr_save_state); when the delays are turned
+ * on the history starts from zeros.  Frames already pushed keep the old
+ * delays.  corr_grad applies them to its own samples from a zero history;
+ * batches (corr_batch_*) reject handles with delays set (CORR_EINVAL). */
+int corr_set_sample_delays(corr_t h, const int32_t* delays);
+
 /* Correlate n samples per antenna (n a multiple of K, n >= 0) and add them
  * to the running integration.  `samples` holds n/K frames in the layout
  * above (n*N/2 bytes).  Host memory is staged through the handle's pinned

@@ -12,8 +12,9 @@ Every function is the plain definition of the quantity the paper computes,
 in float64, with library primitives (a matrix product, numpy's FFT in the
 self-checks) used only as whole steps:
 
-* ``fx``   -- unpack, direct DFT, gain/delay correction, cross-multiply and
-              accumulate (Sec. 1 and Sec. 4 of the paper).
+* ``fx``   -- unpack, integer sample delays of the streaming form, direct
+              DFT, gain/delay correction, cross-multiply and accumulate
+              (Sec. 1 and Sec. 4 of the paper).
 * ``grad`` -- closed-form gradient of the visibility loss with respect to the
               per-antenna gains and delays applied before the cross-multiply.
 
@@ -27,6 +28,7 @@ from .fx import (  # noqa: F401
     baseline_pairs,
     correction_factors,
     correlate,
+    delay_samples,
     dft_matrix,
     spectra,
     unpack,

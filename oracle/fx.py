@@ -181,9 +181,36 @@ def visibilities_channels(packed, N, K, channels, gains=None, delays=None,
     return np.ascontiguousarray(G[:, iu, ju].T), F
 
 
-def correlate(packed, N, K, gains=None, delays=None):
-    """End to end: bytes -> V[P][K/2] and the number of spectra accumulated."""
+# ---------------------------------------------------------------------------
+# Streaming form: coarse integer delays on the sample stream
+# ---------------------------------------------------------------------------
+
+def delay_samples(x, sample_delays):
+    """y_i[t] = x_i[t - D_i] for t >= D_i, 0 before (the stream starts at t = 0).
+
+    Reading (the paper mentions only a phase applied before accumulation,
+    Sec. 2.1; the integer shift is the coarse delay tracking of an FX
+    correlator's streaming input): antenna i's samples are delayed by D_i
+    whole samples, so a common signal that reaches antenna i d_i samples late
+    lines up on every antenna when D_i = max(d) - d_i.
+    """
+    x = np.asarray(x)
+    N, T = x.shape
+    y = np.zeros_like(x)
+    for i in range(N):
+        D = int(sample_delays[i])
+        if D < T:
+            y[i, D:] = x[i, :T - D]          # y[i, t] = x[i, t - D] for t >= D
+    return y
+
+
+def correlate(packed, N, K, gains=None, delays=None, sample_delays=None):
+    """End to end: bytes -> V[P][K/2] and the number of spectra accumulated
+    (with optional integer sample delays on the stream, then the DFT, then the
+    optional gain/phase correction)."""
     x = unpack(packed, N, K)
+    if sample_delays is not None:
+        x = delay_samples(x, sample_delays)
     X = spectra(x, K)
     if gains is not None or delays is not None:
         X = X * correction_factors(K, gains, delays, N=N)[:, None, :]

@@ -55,6 +55,7 @@ _SIGS = {
     "corr_debug_spectra": (_int, [_vp, _vp, _i64, _vp]),
     "corr_correlate_noalloc": (_int, [_vp, _i64, _int, _int, _vp, _vp]),
     "corr_set_scales": (_int, [_vp, _vp]),
+    "corr_set_sample_delays": (_int, [_vp, _vp]),
     "corr_batch_create": (_int, [ctypes.POINTER(_vp), _int, ctypes.POINTER(_int), ctypes.POINTER(_int), _int]),
     "corr_batch_set_chunk": (_int, [_vp, _i64]),
     "corr_batch_set_tiles": (_int, [_vp, _int, _int, _int, _int]),
@@ -178,6 +179,13 @@ def corr_dump(h, vis, fp64=False):
     n = _i64(0)
     _check(_lib.corr_dump(h, _addr(vis), ctypes.byref(n), 1 if fp64 else 0), h)
     return n.value
+
+
+def corr_set_sample_delays(h, delays):
+    """Integer sample delays per antenna (N int32 in [0, K]; None = off)."""
+    if delays is not None and isinstance(delays, (list, tuple, np.ndarray)):
+        delays = np.ascontiguousarray(np.asarray(delays, np.int32))
+    return _check(_lib.corr_set_sample_delays(h, _addr(delays)), h)
 
 
 def corr_dump_async(h, vis, fp64=False):
@@ -331,6 +339,9 @@ class Correlator:
 
     def set_corrections(self, gains=None, delays=None):
         corr_set_corrections(self.h, gains, delays)
+
+    def set_sample_delays(self, delays=None):
+        corr_set_sample_delays(self.h, delays)
 
     def push(self, samples, n=None):
         """``samples``: uint8 buffer [n/K][N][K/2]; n defaults to its size."""

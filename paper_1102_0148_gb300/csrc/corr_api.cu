@@ -61,6 +61,14 @@ struct corr_s {
     cudaEvent_t stage_full[kHostStages] = {};
     int64_t stage_frames = 0;
     int stage_next = 0;
+    // coarse integer sample delays (corr_set_sample_delays)
+    bool sdelay_on = false;
+    int* sdelay = nullptr;          // [N] samples, device
+    std::vector<int> sdelay_host;   // the same, for checkpoints
+    uint8_t* hist[2] = {};          // [N][K/2] last frame of the stream so far (ping-pong)
+    int hist_cur = 0;
+    uint8_t* shifted = nullptr;     // [cap][N][K/2] delayed chunk
+    int64_t shifted_frames = 0;
     void* vis_dev = nullptr;
     int64_t n_spec = 0;
     int64_t fill = 0;            // frames waiting in the workspace for the X-engine
@@ -354,6 +362,13 @@ int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, doubl
             CUDA_TRY(h, cudaEventCreateWithFlags(&h->stage_full[b], cudaEventDisableTiming));
         }
     }
+    if (h->sdelay_on && h->shifted_frames < h->cap) {      // the pass grew since
+        cudaFree(h->shifted);
+        h->shifted = nullptr;
+        h->shifted_frames = 0;
+        CUDA_TRY(h, cudaMalloc((void**)&h->shifted, (size_t)h->cap * rec));
+        h->shifted_frames = h->cap;
+    }
     for (int64_t f0 = 0; f0 < frames;) {
         if (h->fill > 0 && acc != h->fill_acc) {
             int rc = flush(h);
@@ -373,6 +388,16 @@ int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, doubl
             CUDA_TRY(h, cudaEventRecord(h->stage_full[b], h->copy_stream));
             CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->stage_full[b], 0));
             din = h->stage[b];
+        }
+        if (h->sdelay_on) {
+            // the stream's history feeds pushes only; corr_grad's samples
+            // (raw) start from zeros and leave it untouched
+            const uint8_t* hin = raw ? nullptr : h->hist[h->hist_cur];
+            uint8_t* hout = raw ? nullptr : h->hist[h->hist_cur ^ 1];
+            CUDA_TRY(h, launch_sample_delay(din, S, h->N, h->K, h->sdelay, hin, hout, h->shifted,
+                                            h->stream));
+            if (!raw) h->hist_cur ^= 1;
+            din = h->shifted;
         }
         int rc = stage_frames(h, din, S, raw, acc);
         if (rc != CORR_OK) return rc;
@@ -397,6 +422,10 @@ void destroy_impl(corr_t h) {
     cudaFree(h->grad_buf);
     cudaFree(h->status);
     cudaFree(h->vis_dev);
+    cudaFree(h->sdelay);
+    cudaFree(h->hist[0]);
+    cudaFree(h->hist[1]);
+    cudaFree(h->shifted);
     for (int b = 0; b < kHostStages; ++b) {
         cudaFree(h->stage[b]);
         if (h->stage_free[b]) cudaEventDestroy(h->stage_free[b]);
@@ -540,12 +569,45 @@ struct StateHeader {
     uint64_t magic;
     int32_t N, K, dtype, scales_ready;
     int64_t n_spec;
+    int32_t sample_delays, reserved;   // 1: delays [N] int32 and the stream history follow
 };
-constexpr uint64_t kStateMagic = 0x31726f6362677242ull;   // arbitrary tag
+constexpr uint64_t kStateMagic = 0x32726f6362677242ull;   // arbitrary tag
 
 size_t state_bytes(corr_t h) {
     return sizeof(StateHeader) + (size_t)h->C * h->P * sizeof(double2) +
-           (narrow(h) ? (size_t)h->N * h->C * sizeof(float) : 0);
+           (narrow(h) ? (size_t)h->N * h->C * sizeof(float) : 0) +
+           (h->sdelay_on ? (size_t)h->N * sizeof(int32_t) + (size_t)h->N * (h->K / 2) : 0);
+}
+
+// Turn the coarse sample delays on with `d` (host, N entries) or off (all
+// zero); the stream history starts from zeros when they are turned on.
+int apply_sample_delays(corr_t h, const int* d) {
+    bool any = false;
+    for (int i = 0; i < h->N; ++i) any |= d[i] != 0;
+    if (!any) {
+        h->sdelay_on = false;
+        return CORR_OK;
+    }
+    const size_t hb = (size_t)h->N * (h->K / 2);
+    if (!h->sdelay) {
+        CUDA_TRY(h, cudaMalloc((void**)&h->sdelay, h->N * sizeof(int)));
+        for (int b = 0; b < 2; ++b) CUDA_TRY(h, cudaMalloc((void**)&h->hist[b], hb));
+    }
+    if (h->shifted_frames < h->cap) {
+        cudaFree(h->shifted);
+        h->shifted = nullptr;
+        h->shifted_frames = 0;
+        CUDA_TRY(h, cudaMalloc((void**)&h->shifted, (size_t)h->cap * hb));
+        h->shifted_frames = h->cap;
+    }
+    if (!h->sdelay_on) {
+        CUDA_TRY(h, cudaMemsetAsync(h->hist[h->hist_cur], 0, hb, h->stream));
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(h->sdelay, d, h->N * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));    // d may be a caller's temporary
+    h->sdelay_host.assign(d, d + h->N);
+    h->sdelay_on = true;
+    return CORR_OK;
 }
 
 int corr_state_bytes(corr_t h, size_t* bytes) {
@@ -561,14 +623,25 @@ int corr_save_state(corr_t h, void* buf) {
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     int rc = check_status(h);
     if (rc != CORR_OK) return rc;
-    StateHeader hd{kStateMagic, h->N, h->K, h->dtype, h->scales_ready ? 1 : 0, h->n_spec};
+    StateHeader hd{kStateMagic, h->N, h->K, h->dtype, h->scales_ready ? 1 : 0, h->n_spec,
+                   h->sdelay_on ? 1 : 0, 0};
     unsigned char* p = static_cast<unsigned char*>(buf);
     memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
     const size_t ab = (size_t)h->C * h->P * sizeof(double2);
     CUDA_TRY(h, cudaMemcpy(p, h->acc, ab, cudaMemcpyDeviceToHost));
-    if (narrow(h)) CUDA_TRY(h, cudaMemcpy(p + ab, h->scale, (size_t)h->N * h->C * sizeof(float),
-                                          cudaMemcpyDeviceToHost));
+    p += ab;
+    if (narrow(h)) {
+        CUDA_TRY(h, cudaMemcpy(p, h->scale, (size_t)h->N * h->C * sizeof(float),
+                               cudaMemcpyDeviceToHost));
+        p += (size_t)h->N * h->C * sizeof(float);
+    }
+    if (h->sdelay_on) {
+        memcpy(p, h->sdelay_host.data(), h->N * sizeof(int32_t));
+        p += h->N * sizeof(int32_t);
+        CUDA_TRY(h, cudaMemcpy(p, h->hist[h->hist_cur], (size_t)h->N * (h->K / 2),
+                               cudaMemcpyDeviceToHost));
+    }
     return CORR_OK;
 }
 
@@ -586,10 +659,25 @@ int corr_load_state(corr_t h, const void* buf) {
     const unsigned char* p = static_cast<const unsigned char*>(buf) + sizeof hd;
     const size_t ab = (size_t)h->C * h->P * sizeof(double2);
     CUDA_TRY(h, cudaMemcpy(h->acc, p, ab, cudaMemcpyHostToDevice));
-    if (narrow(h) && hd.scales_ready) {
-        CUDA_TRY(h, cudaMemcpy(h->scale, p + ab, (size_t)h->N * h->C * sizeof(float),
+    p += ab;
+    if (narrow(h)) {
+        if (hd.scales_ready) {
+            CUDA_TRY(h, cudaMemcpy(h->scale, p, (size_t)h->N * h->C * sizeof(float),
+                                   cudaMemcpyHostToDevice));
+            h->scales_ready = true;
+        }
+        p += (size_t)h->N * h->C * sizeof(float);
+    }
+    if (hd.sample_delays) {
+        std::vector<int> d(h->N);
+        memcpy(d.data(), p, h->N * sizeof(int32_t));
+        p += h->N * sizeof(int32_t);
+        int rc = apply_sample_delays(h, d.data());
+        if (rc != CORR_OK) return rc;
+        CUDA_TRY(h, cudaMemcpy(h->hist[h->hist_cur], p, (size_t)h->N * (h->K / 2),
                                cudaMemcpyHostToDevice));
-        h->scales_ready = true;
+    } else {
+        h->sdelay_on = false;
     }
     h->n_spec = hd.n_spec;
     return CORR_OK;
@@ -600,6 +688,25 @@ int corr_test_fault(corr_t h, int kind, double wait_limit_s) {
     if (kind != 1) return set_err(h, CORR_EINVAL, "unknown fault kind %d", kind);
     if (!h->use_tc) return set_err(h, CORR_EINVAL, "the withheld-copy fault needs a tensor-core handle");
     return tc_test_withhold(h->tc, wait_limit_s, h->err);
+}
+
+int corr_set_sample_delays(corr_t h, const int32_t* delays) {
+    if (!h) return CORR_EINVAL;
+    std::vector<int> d(h->N, 0);
+    if (delays) {
+        if (is_device_ptr(delays)) {
+            CUDA_TRY(h, cudaMemcpy(d.data(), delays, h->N * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        } else {
+            memcpy(d.data(), delays, h->N * sizeof(int32_t));
+        }
+        for (int i = 0; i < h->N; ++i)
+            if (d[i] < 0 || d[i] > h->K)
+                return set_err(h, CORR_EINVAL, "sample delay %d of antenna %d is outside [0, K=%d]",
+                               d[i], i, h->K);
+    }
+    int frc = flush(h);                  // frames already pushed keep the old delays
+    if (frc != CORR_OK) return frc;
+    return apply_sample_delays(h, d.data());
 }
 
 int corr_set_corrections(corr_t h, const float* gains, const float* delays) {
@@ -883,6 +990,9 @@ void batch_free_graph(corr_batch_t b) {
 }
 
 int batch_check(corr_batch_t b, const uint8_t* const* samples, const int64_t* n) {
+    for (int m = 0; m < b->n; ++m)
+        if (b->h[m]->sdelay_on)
+            return batch_err(b, CORR_EINVAL, "a mode has sample delays set; batches do not apply them");
     if (!samples || !n) return batch_err(b, CORR_EINVAL, "NULL argument");
     for (int m = 0; m < b->n; ++m) {
         if (n[m] < 0 || n[m] % b->h[m]->K)

@@ -62,6 +62,14 @@ struct FengineArgs {
 
 cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st);
 
+// Coarse integer delays on the packed stream: out = in delayed by delays[i]
+// samples (0..K) per antenna, S frames [S][N][K/2].  The frame before the
+// chunk comes from hist_in ([N][K/2], zeros when NULL); the chunk's last
+// frame is copied to hist_out when it is not NULL.
+cudaError_t launch_sample_delay(const uint8_t* in, int64_t S, int N, int K, const int* delays,
+                                const uint8_t* hist_in, uint8_t* hist_out, uint8_t* out,
+                                cudaStream_t st);
+
 // Correction table a[i][k] = g_i exp(-2 pi i k tau_i / K), computed in FP64.
 cudaError_t launch_correction_table(const float2* gains, const float* delays, int N, int K,
                                     float2* table, cudaStream_t st);

@@ -14,6 +14,8 @@
 
 #include <cuda_fp8.h>
 
+#include <algorithm>
+
 namespace gbcorr {
 namespace {
 
@@ -833,11 +835,133 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Coarse integer delays: y_i[t] = x_i[t - D_i], 0 <= D_i <= K, on the packed
+// 4-bit stream before the F-engine.  A CTA takes frames s0 .. s0 + FB - 1 of
+// one antenna plus the frame before them (from the previous chunk's last
+// frame, `hist_in`, when s0 = 0; zeros without it) into shared memory and
+// writes each output byte's two samples from their delayed positions.  The
+// CTA holding the chunk's last frame copies it to `hist_out` for the next
+// chunk.
+// ---------------------------------------------------------------------------
+
+constexpr int kDelayThreads = 256;
+constexpr int kDelayLoads = 8;      // loads in flight per thread
+
+template <int V>
+struct DelayVec;
+template <>
+struct DelayVec<4> {
+    using T = uint4;
+};
+template <>
+struct DelayVec<2> {
+    using T = uint2;
+};
+
+// V 32-bit words per thread and step (4 when a frame is a multiple of 16
+// bytes, else 2): every frame of the CTA is copied in V-word chunks.
+template <int V>
+__global__ void __launch_bounds__(kDelayThreads) sample_delay_kernel(
+    const uint8_t* __restrict__ in, int64_t S, int N, int K, const int* __restrict__ D,
+    const uint8_t* __restrict__ hist_in, uint8_t* __restrict__ hist_out, uint8_t* __restrict__ out,
+    int FB, int cshift, int aligned) {
+    using Vec = typename DelayVec<V>::T;
+    extern __shared__ __align__(16) uint8_t dbuf[];      // [FB + 1][K/2] (+ 16 bytes)
+    const int L = K >> 1;
+    const int wl = L >> 2;                               // 32-bit words per frame
+    const int cl = 1 << cshift;                          // V-word chunks per frame
+    const int i = blockIdx.y;
+    const int64_t s0 = (int64_t)blockIdx.x * FB;
+    const int nf = (int)min((int64_t)FB, S - s0);
+    const int d = __ldg(D + i);
+    const int64_t NL = (int64_t)N * L;                   // bytes from one frame to the next
+    uint32_t* b32 = reinterpret_cast<uint32_t*>(dbuf);
+    // frames s0 - 1 .. s0 + nf - 1 of antenna i; the loads of a thread are
+    // issued together (kDelayLoads at a time), then stored
+    const uint8_t* first = in + (s0 * N + i) * (int64_t)L - NL;   // frame s0 - 1
+    const int chunks = (nf + 1) << cshift;
+    for (int c0 = threadIdx.x; c0 < chunks; c0 += kDelayThreads * kDelayLoads) {
+        Vec v[kDelayLoads];
+#pragma unroll
+        for (int u = 0; u < kDelayLoads; ++u) {
+            const int c = c0 + u * kDelayThreads;
+            uint32_t* vw = reinterpret_cast<uint32_t*>(&v[u]);
+#pragma unroll
+            for (int k = 0; k < V; ++k) vw[k] = 0u;
+            if (c < chunks) {
+                const int f = c >> cshift;
+                const int b = (c & (cl - 1)) * 4 * V;
+                if (f > 0 || s0 > 0) {
+                    const uint8_t* src = first + f * NL + b;
+                    if (aligned) {
+                        v[u] = __ldg(reinterpret_cast<const Vec*>(src));
+                    } else {
+                        for (int k = 0; k < 4 * V; ++k)
+                            vw[k >> 2] |= (uint32_t)src[k] << (8 * (k & 3));
+                    }
+                } else if (hist_in) {
+                    v[u] = *reinterpret_cast<const Vec*>(hist_in + (int64_t)i * L + b);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kDelayLoads; ++u) {
+            const int c = c0 + u * kDelayThreads;
+            if (c < chunks) reinterpret_cast<Vec*>(b32)[c] = v[u];
+        }
+    }
+    if (threadIdx.x < 4) b32[(nf + 1) * wl + threadIdx.x] = 0u;   // read past the end, never used
+    __syncthreads();
+    // Output sample u of the CTA's frames is buffer sample K + u - d: a shift
+    // by the same Q0 bytes (+ a nibble when d is odd) for every output word.
+    const int Q0 = L - ((d + 1) >> 1);
+    const int wb = Q0 >> 2;
+    const int sh = ((Q0 & 3) << 3) + ((d & 1) << 2);
+    uint8_t* obase = out + (s0 * N + i) * (int64_t)L;
+    for (int c = threadIdx.x; c < (nf << cshift); c += kDelayThreads) {
+        const int f = c >> cshift;
+        const int w = c * V;
+        uint32_t a[V + 1];
+#pragma unroll
+        for (int k = 0; k <= V; ++k) a[k] = b32[wb + w + k];
+        Vec o;
+        uint32_t* ow = reinterpret_cast<uint32_t*>(&o);
+#pragma unroll
+        for (int k = 0; k < V; ++k) ow[k] = __funnelshift_r(a[k], a[k + 1], sh);
+        *reinterpret_cast<Vec*>(obase + f * NL + (c & (cl - 1)) * 4 * V) = o;
+    }
+    if (hist_out && s0 + nf == S)
+        for (int w = threadIdx.x; w < wl; w += kDelayThreads)
+            reinterpret_cast<uint32_t*>(hist_out + (int64_t)i * L)[w] = b32[nf * wl + w];
+}
+
 cudaError_t launch_correction_table(const float2* gains, const float* delays, int N, int K,
                                     float2* table, cudaStream_t st) {
     const int64_t total = (int64_t)N * (K / 2);
     const int blocks = (int)((total + 255) / 256);
     correction_table_kernel<<<blocks, 256, 0, st>>>(gains, delays, N, K, table);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_delay(const uint8_t* in, int64_t S, int N, int K, const int* delays,
+                                const uint8_t* hist_in, uint8_t* hist_out, uint8_t* out,
+                                cudaStream_t st) {
+    if (S <= 0) return cudaSuccess;
+    const int L = K / 2;
+    const int V = (L % 16 == 0) ? 4 : 2;
+    int cshift = 0;
+    while ((4 * V << cshift) < L) ++cshift;
+    const int FB = std::max(1, 16384 / L);     // 64 frames at K = 512
+    const size_t smem = (size_t)(FB + 1) * L + 16;
+    const int aligned = (reinterpret_cast<uintptr_t>(in) & (4 * V - 1)) == 0 ? 1 : 0;
+    dim3 grid((unsigned)((S + FB - 1) / FB), (unsigned)N);
+    if (V == 4)
+        sample_delay_kernel<4><<<grid, kDelayThreads, smem, st>>>(in, S, N, K, delays, hist_in,
+                                                                  hist_out, out, FB, cshift, aligned);
+    else
+        sample_delay_kernel<2><<<grid, kDelayThreads, smem, st>>>(in, S, N, K, delays, hist_in,
+                                                                  hist_out, out, FB, cshift, aligned);
     return cudaGetLastError();
 }
 

@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(kF1024Threads, 2) fengine_k1024(FengineArgs a)
     float2* xch = reinterpret_cast<float2*>(stg + (DEBUG ? 0 : kStg1024Floats));  // [8][16][33]
     float2* tw_stage = xch + 8 * 16 * kX1024Stride;                         // [16 k1][32 t]
     float2* tw_post = tw_stage + 512;                                       // [512]
-    float2* tw32 = tw_post + 512;                                           // [16] W32^{t'}
+    float2* tw32 = tw_post + 512;                                           // [2][16]
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -423,7 +423,8 @@ __global__ void __launch_bounds__(kF1024Threads, 2) fengine_k1024(FengineArgs a)
         const float2 w = a.twiddle[e];
         tw_post[e] = make_float2(0.5f * post * w.y, -0.5f * post * w.x);
     }
-    if (tid < 16) tw32[tid] = a.twiddle[32 * tid];         // W32^{t'} = W1024^{32 t'}
+    // [2][16]: ones, then W32^{t'} = W1024^{32 t'}
+    if (tid < 32) tw32[tid] = tid < 16 ? make_float2(1.0f, 0.0f) : a.twiddle[32 * (tid - 16)];
     const float chalf = 0.5f * post;
 
     uint4 raw0 = make_uint4(0u, 0u, 0u, 0u), raw1 = raw0;
@@ -460,18 +461,17 @@ __global__ void __launch_bounds__(kF1024Threads, 2) fengine_k1024(FengineArgs a)
         for (int t = 0; t < 16; ++t) x[t] = gx[k1 * kX1024Stride + 16 * hh + t];
         __syncwarp();
         // radix 2 across the half-warps: half 0 forms B_t' + B_t'+16, half 1
-        // W32^{t'} (B_t' - B_t'+16)
+        // W32^{t'} (B_t' - B_t'+16).  Both halves run the same instructions,
+        // y + sgn x times a twiddle row that is all ones for half 0.
+        const float sgn = hh ? -1.0f : 1.0f;
+        const float2* twh = tw32 + 16 * hh;
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
             float2 y;
             y.x = __shfl_xor_sync(0xffffffffu, x[t].x, 16);
             y.y = __shfl_xor_sync(0xffffffffu, x[t].y, 16);
-            if (hh == 0) {
-                x[t] = cadd(x[t], y);
-            } else {
-                x[t] = csub(y, x[t]);
-                if (t > 0) x[t] = cmul(x[t], tw32[t]);
-            }
+            const float2 v = make_float2(fmaf(sgn, x[t].x, y.x), fmaf(sgn, x[t].y, y.y));
+            x[t] = t > 0 ? cmul(v, twh[t]) : v;
         }
         dft16(x);
         // x[q] = Z[k1 + 16 hh + 32 q]; partner Z[512 - k]
@@ -767,7 +767,7 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
         const int64_t fr = dbg ? a.S : a.S_pad;
         if (fr <= 0) return cudaSuccess;
         dim3 grid((unsigned)((fr + kF1024Frames - 1) / kF1024Frames), (unsigned)a.N);
-        const size_t tables = ((size_t)8 * 16 * kX1024Stride + 512 + 512 + 16) * sizeof(float2);
+        const size_t tables = ((size_t)8 * 16 * kX1024Stride + 512 + 512 + 32) * sizeof(float2);
         const size_t smem = dbg ? tables : tables + (size_t)kStg1024Floats * sizeof(float);
         auto go = [&](auto kern) -> cudaError_t {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -63,7 +63,7 @@ struct TcModeArgs {
     int N, C, P;
     int nblk, npairs;         // antenna blocks of 64 and their pairs b1 <= b2
     int n_split;
-    int item_base, n_items;   // items: channel fastest, then block pair, then split
+    int item_base, n_items;   // items: block pair fastest, then channel, then split
     int64_t S_pad, S_item;
     int64_t tiles;            // k-tiles of the pass (balanced deal)
     uint32_t box_bytes;       // bytes one TMA box of this mode lands in shared memory
@@ -128,11 +128,13 @@ __device__ __forceinline__ Item decode_item(const TcArgs& a, int g) {
     int l = g - d.item_base;
     Item it;
     it.m = m;
-    it.k = l % d.C;
-    l /= d.C;
+    // block pair fastest: the CTAs that take one channel's pairs at the same
+    // time share its block tiles through L2
     int pr = l % d.npairs;
+    l /= d.npairs;
     it.pr = pr;
-    it.sp = l / d.npairs;
+    it.k = l % d.C;
+    it.sp = l / d.C;
     int b1 = 0;
     while (pr >= d.nblk - b1) {
         pr -= d.nblk - b1;
@@ -1050,11 +1052,10 @@ DealPlan choose_deal(TcPlan* const* plans, int n, const int64_t* S_pad) {
             const int64_t per = (tiles + sp[m] - 1) / sp[m];
             for (int s = 0; s < sp[m]; ++s) {
                 const int64_t t = std::min<int64_t>(per, tiles - (int64_t)s * per);
-                for (int pr = 0; pr < p->npairs; ++pr) {
-                    const double w = (double)t * 0.5 * host_pair_units(pr, p->nblk) + 4.0 +
-                                     (sp[m] > 1 ? 2.0 : 0.0);
-                    for (int k = 0; k < p->C; ++k, ++g) load[g % sms] += w;
-                }
+                for (int k = 0; k < p->C; ++k)
+                    for (int pr = 0; pr < p->npairs; ++pr, ++g)
+                        load[g % sms] += (double)t * 0.5 * host_pair_units(pr, p->nblk) + 4.0 +
+                                         (sp[m] > 1 ? 2.0 : 0.0);
             }
         }
         const double score = *std::max_element(load.begin(), load.end());
@@ -1083,7 +1084,10 @@ DealPlan choose_deal(TcPlan* const* plans, int n, const int64_t* S_pad) {
     // (one mode only: with several, the round-robin deal spreads every mode's
     // items, whose ends differ in cost, evenly over the CTAs -- measured
     // faster on the four-mode batch)
-    if (n == 1 && units > 0 && cap_slots >= 3) {
+    // (single antenna block only: with several, the round-robin deal hands one
+    // channel's block pairs to neighbouring CTAs at once, which then share its
+    // tiles through L2; contiguous shares would read them from HBM per pair)
+    if (n == 1 && plans[0]->nblk == 1 && units > 0 && cap_slots >= 3) {
         int64_t G = sms;
         if (max_span > 0)
             G = std::min<int64_t>(G, std::max<int64_t>(1, (int64_t)(cap_slots - 2) * units / max_span));

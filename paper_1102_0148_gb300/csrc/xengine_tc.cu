@@ -979,12 +979,16 @@ LaunchShape launch_shape(TcPlan* const* plans, int n) {
         const size_t sb = (size_t)plans[0]->planes * atoms * slot * (L.two_tiles ? 2 : 1);
         return std::min<int>(16, (int)((kSmemBudget - fixed) / sb));
     };
-    // k-tiles per stage: as many (up to 4) as still leave 3 stages, unless set
+    // k-tiles per stage, unless set: as many (up to 4) as still leave 3
+    // stages; with two tiles per k-tile (several antenna blocks) 2 stages
+    // suffice -- each stage handshake costs a fixed latency, measured at
+    // N = 256: 2 x 2 k-tiles 1.10 ms against 4 x 1 k-tile 1.24 ms per pass
     L.atoms = plans[0]->atoms;
     if (!L.atoms) {
         L.atoms = 1;
+        const int min_stages = L.two_tiles ? 2 : 3;
         for (int at = 4; at > 1; at /= 2)
-            if (fit(at) >= 3) {
+            if (fit(at) >= min_stages) {
                 L.atoms = at;
                 break;
             }

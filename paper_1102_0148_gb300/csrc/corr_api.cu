@@ -230,8 +230,7 @@ int estimate_scales(corr_t h, const uint8_t* din, int64_t S) {
     return CORR_OK;
 }
 
-// One workspace pass: S frames at `din` (device) -> `acc`.  raw = true skips
-// the per-antenna corrections (the uncorrected visibilities for corr_grad).
+// S frames rounded up to whole kSpecPad-frame blocks (the padding frames are zero).
 int64_t pad_frames(int64_t S) { return (S + kSpecPad - 1) / kSpecPad * kSpecPad; }
 
 // F-engine half of a pass: S frames at `din` -> the workspace.
@@ -308,12 +307,6 @@ int xengine_pass(corr_t h, int64_t S_pad, double2* acc) {
         prof_end(h, CORR_KERNEL_REDUCE);
     }
     return CORR_OK;
-}
-
-int run_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, double2* acc) {
-    int rc = fengine_pass(h, din, S, raw);
-    if (rc != CORR_OK) return rc;
-    return xengine_pass(h, pad_frames(S), acc);
 }
 
 // X-engine over the frames waiting in the workspace.

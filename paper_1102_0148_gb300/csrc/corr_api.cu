@@ -233,7 +233,9 @@ int estimate_scales(corr_t h, const uint8_t* din, int64_t S) {
 // S frames rounded up to whole kSpecPad-frame blocks (the padding frames are zero).
 int64_t pad_frames(int64_t S) { return (S + kSpecPad - 1) / kSpecPad * kSpecPad; }
 
-// F-engine half of a pass: S frames at `din` -> the workspace.
+// F-engine of S frames at `din` (device) into the workspace from frame `off`;
+// raw = true skips the per-antenna corrections (the uncorrected visibilities
+// corr_grad needs).
 int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off = 0) {
     const int64_t S_pad = pad_frames(S);
     if (narrow(h) && !h->scales_ready) {

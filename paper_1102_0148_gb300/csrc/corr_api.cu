@@ -17,13 +17,19 @@ using namespace gbcorr;
 
 namespace {
 
-// Default workspace: 8192 frames (four 2^20-sample pushes at K = 512), fewer
-// when that would exceed 2 GiB, but at least 2048.
+// Default workspace of the tensor-core handles: as many frames as fit in
+// 8 GiB, at most 131072 (a 1 s integration at 35 MS/s and K = 512 is one
+// pass; the X-engine's per-pass costs shrink with the pass) and at least
+// 2048.  The CUDA-core X-engine keeps 8192 frames within 2 GiB (its FP32
+// partials grow with the pass).
 constexpr int64_t kDefaultChunk = 8192;
+constexpr int64_t kMaxTcChunk = 131072;
 constexpr int64_t kMinDefaultChunk = 2048;
 constexpr size_t kDefaultWorkspaceBytes = (size_t)2 << 30;
+constexpr size_t kTcWorkspaceBytes = (size_t)8 << 30;
 constexpr int64_t kSimtSplit = 256;   // frames per SIMT X-engine split
-constexpr int kHostStages = 4;         // device staging buffers for host input
+constexpr int kHostStages = 16;        // device staging buffers for host input
+constexpr size_t kStageBytes = (size_t)32 << 20;   // ~32 MB each
 
 thread_local std::string g_create_error = "no error";
 
@@ -136,7 +142,10 @@ int alloc_workspace(corr_t h, int64_t cap) {
     cap = (cap + kSpecPad - 1) / kSpecPad * kSpecPad;
     const size_t eb = (size_t)spec_elem_bytes(h->spec_type);
     const size_t spec_bytes = (size_t)spec_planes(h->spec_type) * h->C * 2 * h->N * cap * eb;
-    const int max_split = (int)((cap + kSimtSplit - 1) / kSimtSplit);
+    // FP32 partials: one per 256-frame split for the CUDA-core X-engine, at
+    // most 8 slots for the tensor cores (their planner's limit)
+    int max_split = (int)((cap + kSimtSplit - 1) / kSimtSplit);
+    if (h->use_tc) max_split = std::min(max_split, 8);
     void* spec = nullptr;
     float2* part = nullptr;
     cudaError_t e = cudaMalloc(&spec, spec_bytes);
@@ -250,8 +259,8 @@ int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off 
     fa.S_pad = S_pad;
     fa.twiddle = h->twiddle;
     fa.corr = (h->corr_on && !raw) ? h->corr_tab : nullptr;
-    fa.spec = static_cast<unsigned char*>(h->spec) + off * spec_elem_bytes(h->spec_type);
-    fa.ld = h->cap;
+    fa.spec = h->spec;
+    fa.s_base = off;
     fa.plane_stride = (int64_t)h->C * 2 * h->N * h->cap;
     fa.spec_type = h->spec_type;
     fa.scale = (h->spec_type == SPEC_F16 || h->spec_type == SPEC_F8) ? h->scale : nullptr;
@@ -290,7 +299,6 @@ int xengine_pass(corr_t h, int64_t S_pad, double2* acc) {
     } else {
         XengineArgs xa{};
         xa.spec = h->spec;
-        xa.ld = h->cap;
         xa.N = h->N;
         xa.C = h->C;
         xa.S_pad = S_pad;
@@ -348,9 +356,11 @@ int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, doubl
     const int64_t rec = (int64_t)h->N * (h->K / 2);
     const bool host = !is_device_ptr(samples);
     if (host && !h->stage[0]) {
-        // half a workspace pass per buffer (whole 128-frame blocks), so a
-        // pass's copies can run while the X-engine works on the previous one
-        h->stage_frames = std::max<int64_t>(kSpecPad, h->cap / 2 / kSpecPad * kSpecPad);
+        // ~32 MB per buffer (whole 128-frame blocks), 16 of them: the copies
+        // (~205 GB/s from pinned host memory) can run ~2.5 ms ahead of the
+        // F-engine, across an X-engine pass of a whole integration
+        h->stage_frames = std::max<int64_t>(
+            kSpecPad, std::min<int64_t>(h->cap, (int64_t)(kStageBytes / rec)) / kSpecPad * kSpecPad);
         for (int b = 0; b < kHostStages; ++b) {
             CUDA_TRY(h, cudaMalloc((void**)&h->stage[b], (size_t)(h->stage_frames * rec)));
             CUDA_TRY(h, cudaEventCreateWithFlags(&h->stage_free[b], cudaEventDisableTiming));
@@ -518,10 +528,16 @@ int corr_create(corr_t* out, int N, int K, int dtype) {
             cudaSuccess)
             return bail(set_err(h, CORR_ECUDA, "initialisation copy failed"));
     }
-    int64_t chunk = kDefaultChunk;
     const size_t per_frame = (size_t)spec_planes(h->spec_type) * h->C * 2 * h->N *
                              spec_elem_bytes(h->spec_type);
-    while (chunk > kMinDefaultChunk && (size_t)chunk * per_frame > kDefaultWorkspaceBytes) chunk /= 2;
+    int64_t chunk = kDefaultChunk;
+    if (h->use_tc) {
+        chunk = (int64_t)(kTcWorkspaceBytes / per_frame) / kSpecPad * kSpecPad;
+        chunk = std::max(kMinDefaultChunk, std::min(kMaxTcChunk, chunk));
+    } else {
+        while (chunk > kMinDefaultChunk && (size_t)chunk * per_frame > kDefaultWorkspaceBytes)
+            chunk /= 2;
+    }
     int rc = alloc_workspace(h, chunk);
     if (rc != CORR_OK) return bail(rc);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess)

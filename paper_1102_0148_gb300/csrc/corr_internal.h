@@ -41,6 +41,21 @@ constexpr float kSplitScale = 0.0625f;
 // so every X-engine tile along the spectrum axis is whole.
 constexpr int kSpecPad = 128;
 
+// Workspace layout, tile-major along the spectra: frames come in tiles of
+// 128 bytes (32 FP32, 64 FP16, 128 FP8 values -- one tensor-core k-tile), and
+// element (k, r, s) of a plane sits at ((s / T * C + k) * 2N + r) * T + s % T.
+// One (tile, channel) holds all 2N rows contiguously, so the X-engine reads a
+// k-tile of a channel as one block and an F-engine CTA's frames of every
+// channel lie within one tile's few megabytes.  Planes (SPEC_F16X2) are
+// plane_stride = C * 2N * cap elements apart.
+inline __host__ __device__ int spec_tile_shift(int t) {
+    return t == SPEC_F32 ? 5 : ((t == SPEC_F16 || t == SPEC_F16X2) ? 6 : 7);
+}
+__host__ __device__ __forceinline__ int64_t spec_off(int k, int r, int64_t s, int N, int C,
+                                                     int tshift) {
+    return ((((s >> tshift) * C + k) * (2 * N) + r) << tshift) + (s & ((1 << tshift) - 1));
+}
+
 // Arguments of one F-engine pass over S frames of one input buffer.
 struct FengineArgs {
     const uint8_t* in;       // [S][N][K/2] packed bytes (device)
@@ -49,10 +64,10 @@ struct FengineArgs {
     int64_t S_pad;           // frames written (>= S; the extra ones are zero)
     const float2* twiddle;   // W_K^m = exp(-2 pi i m / K), m in [0, K)
     const float2* corr;      // [N][K/2] correction a_i[k], or nullptr
-    // Corner-turned workspace: element (k, r, s) at ((k*2N + r) * ld + s),
-    // r < N real parts, r >= N imaginary parts of antenna r mod N.
+    // Corner-turned workspace (spec_off): row r = spec_row(plane, antenna),
+    // frames s_base .. s_base + S_pad - 1 of it written by this pass.
     void* spec;
-    int64_t ld;
+    int64_t s_base;
     int64_t plane_stride;    // elements from the hi plane to the lo plane (SPEC_F16X2)
     int spec_type;
     const float* scale;      // [N][K/2] pre-cast scale (FP16/FP8 only)
@@ -76,8 +91,7 @@ cudaError_t launch_correction_table(const float2* gains, const float* delays, in
 
 // SIMT X-engine over one workspace pass: partial[split][k][p] (FP32 complex).
 struct XengineArgs {
-    const void* spec;
-    int64_t ld;
+    const void* spec;        // FP32 workspace (spec_off), frames from 0
     int N, C;
     int64_t S_pad;           // frames present (multiple of kSpecPad)
     int spec_type;

@@ -131,7 +131,8 @@ __global__ void __launch_bounds__(kThreads) fengine_generic(FengineArgs a, int F
             if (f >= nfr) continue;
             const int plane = row / C;
             const int k = row - plane * C;
-            const int64_t off = ((int64_t)k * 2 * a.N + spec_row(plane, i, a.N)) * a.ld + s0 + f;
+            const int64_t off = spec_off(k, spec_row(plane, i, a.N), a.s_base + s0 + f, a.N, C,
+                                         spec_tile_shift(a.spec_type));
             store_spec(a.spec, a.spec_type, off, stg[row * FT + f], a.plane_stride);
         }
     }
@@ -369,7 +370,8 @@ __global__ void __launch_bounds__(kF512Threads, 2) fengine_k512(FengineArgs a) {
         const int plane = row >> 8;
         const int k = row & 255;
         const float* src = stg + 4 * m * kStgRow + row;
-        const int64_t off = ((int64_t)k * 2 * a.N + spec_row(plane, i, a.N)) * a.ld + s0 + 4 * m;
+        const int64_t off = spec_off(k, spec_row(plane, i, a.N), a.s_base + s0 + 4 * m, a.N,
+                                     a.K >> 1, spec_tile_shift(OUT));
         store4<OUT>(a.spec, off, a.plane_stride, src[0], src[kStgRow], src[2 * kStgRow],
                     src[3 * kStgRow]);
     }
@@ -516,7 +518,8 @@ __global__ void __launch_bounds__(kF1024Threads, 2) fengine_k1024(FengineArgs a)
         const int plane = row >> 9;
         const int k = row & 511;
         const float* src = stg + 4 * m * kStg1024Row + row;
-        const int64_t off = ((int64_t)k * 2 * a.N + spec_row(plane, i, a.N)) * a.ld + s0 + 4 * m;
+        const int64_t off = spec_off(k, spec_row(plane, i, a.N), a.s_base + s0 + 4 * m, a.N,
+                                     a.K >> 1, spec_tile_shift(OUT));
         store4<OUT>(a.spec, off, a.plane_stride, src[0], src[kStg1024Row], src[2 * kStg1024Row],
                     src[3 * kStg1024Row]);
     }
@@ -713,7 +716,8 @@ __global__ void __launch_bounds__(kRadThreads, 1) fengine_rad16(FengineArgs a) {
         const int plane = row / L;
         const int k = row - plane * L;
         const float* src = stg + 4 * m * SR + row;
-        const int64_t off = ((int64_t)k * 2 * a.N + spec_row(plane, i, a.N)) * a.ld + s0 + 4 * m;
+        const int64_t off = spec_off(k, spec_row(plane, i, a.N), a.s_base + s0 + 4 * m, a.N,
+                                     a.K >> 1, spec_tile_shift(OUT));
         store4<OUT>(a.spec, off, a.plane_stride, src[0], src[SR], src[2 * SR], src[3 * SR]);
     }
 }

@@ -35,7 +35,7 @@ constexpr int64_t kMaxPass = 2048;  // frames per pass at most
 size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Scratch layout for one pass of S frames (S a multiple of kSpecPad):
-// twiddles | FP64 accumulator [C][P] | partials [splits][C][P] | spectra [C][2N][S].
+// twiddles | FP64 accumulator [C][P] | partials [splits][C][P] | spectra (tile-major workspace, 32-frame tiles).
 size_t scratch_bytes(int N, int K, int64_t S) {
     const size_t C = (size_t)K / 2, P = (size_t)N * (N + 1) / 2;
     const size_t splits = (size_t)((S + kSplit - 1) / kSplit);
@@ -138,14 +138,13 @@ extern "C" int corr_correlate_noalloc(const uint8_t* samples, int64_t n, int N, 
         fa.twiddle = tw;
         fa.corr = nullptr;
         fa.spec = spec;
-        fa.ld = S_pass;
+        fa.s_base = 0;
         fa.spec_type = SPEC_F32;
         fa.scale = nullptr;
         fa.debug_out = nullptr;
         if ((e = launch_fengine(fa, st)) != cudaSuccess) return fail_cuda(e, "F-engine");
         XengineArgs xa{};
         xa.spec = spec;
-        xa.ld = S_pass;
         xa.N = N;
         xa.C = C;
         xa.S_pad = S_pad;

@@ -43,14 +43,16 @@ __global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt) {
 
     const int64_t sb = (int64_t)split * a.s_per_split;
     const int64_t se = min(a.S_pad, sb + a.s_per_split);
-    const float* base = static_cast<const float*>(a.spec) + (int64_t)k * 2 * N * a.ld;
+    static_assert(kTS == 32, "one 32-frame FP32 workspace tile per step");
 
     for (int64_t s0 = sb; s0 < se; s0 += kTS) {
         __syncthreads();
+        // the tile's 2N rows x 32 frames of channel k are contiguous
+        const float* base = static_cast<const float*>(a.spec) + spec_off(k, 0, s0, N, a.C, 5);
         for (int e = threadIdx.x; e < 2 * N * kTS; e += blockDim.x) {
             const int r = e / kTS;
             const int c = e - r * kTS;
-            const float v = base[(int64_t)r * a.ld + s0 + c];
+            const float v = base[e];
             // row r -> (plane, antenna) under the 64-antenna block layout
             const int b = r >> 7;
             const int w = r & 127;

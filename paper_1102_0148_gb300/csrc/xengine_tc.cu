@@ -66,6 +66,7 @@ struct TcModeArgs {
     int item_base, n_items;   // items: block pair fastest, then channel, then split
     int64_t S_pad, S_item;
     int64_t tiles;            // k-tiles of the pass (balanced deal)
+    int cap_tiles;            // k-tiles of a workspace plane (the lo plane's first tile)
     uint32_t box_bytes;       // bytes one TMA box of this mode lands in shared memory
     int64_t unit_base;        // first work unit of this mode (balanced deal)
     float2* partial;          // [n_split][C][P] FP32 partials (n_split > 1)
@@ -300,12 +301,14 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile
     }
 }
 
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
-                                            int c0, int c1, int c2) {
+// Box (all frames of one k-tile, rows c1 .., channel c2, plane-and-tile c3)
+// of the tile-major workspace.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c1, int c2, int c3) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(0), "r"(c1), "r"(c2), "r"(c3)
         : "memory");
 }
 
@@ -467,14 +470,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                     mbar_expect_tx(fb, bytes);
                     const uint32_t dst = smem_u32(stages + st * stage_bytes);
                     for (int at = 0; at < n_at; ++at) {
-                        const int sa = (int)s + at * a.KT;
+                        const int st4 = (int)(s >> a.kt_shift) + at;   // k-tile of the pass
                         const uint32_t o = (uint32_t)at * atom_bytes;
-                        tma_load_3d(dst + o, map, fb, sa, ra, itm.k);
-                        if (planes == 2) tma_load_3d(dst + plane_off + o, map, fb, sa, ra, d.C + itm.k);
+                        tma_load_4d(dst + o, map, fb, ra, itm.k, st4);
+                        if (planes == 2)
+                            tma_load_4d(dst + plane_off + o, map, fb, ra, itm.k, d.cap_tiles + st4);
                         if (!diag) {
-                            tma_load_3d(dst + tile_set + o, map, fb, sa, rb, itm.k);
+                            tma_load_4d(dst + tile_set + o, map, fb, rb, itm.k, st4);
                             if (planes == 2)
-                                tma_load_3d(dst + tile_set + plane_off + o, map, fb, sa, rb, d.C + itm.k);
+                                tma_load_4d(dst + tile_set + plane_off + o, map, fb, rb, itm.k,
+                                            d.cap_tiles + st4);
                         }
                     }
                     armed |= 1u << st;
@@ -897,13 +902,17 @@ int tc_plan_update(TcPlan* p, void* spec, int64_t cap, int N, int C, int spec_ty
     (void)C;
     const int eb = spec_elem_bytes(spec_type);
     const int R2 = 2 * p->N;
-    cuuint64_t dims[3] = {(cuuint64_t)cap, (cuuint64_t)R2, (cuuint64_t)p->planes * p->C};
-    cuuint64_t strides[2] = {(cuuint64_t)cap * eb, (cuuint64_t)R2 * cap * eb};
-    cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / eb), (cuuint32_t)p->box_rows, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
+    // tile-major workspace: [plane][cap/T tiles][C][2N rows][T frames], T = KT
+    const int T = kRowBytes / eb;
+    cuuint64_t dims[4] = {(cuuint64_t)T, (cuuint64_t)R2, (cuuint64_t)p->C,
+                          (cuuint64_t)p->planes * (cap / T)};
+    cuuint64_t strides[3] = {(cuuint64_t)T * eb, (cuuint64_t)R2 * T * eb,
+                             (cuuint64_t)p->C * R2 * T * eb};
+    cuuint32_t box[4] = {(cuuint32_t)T, (cuuint32_t)p->box_rows, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUtensorMapDataType dt =
         eb == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
-    CUresult r = get_encoder()(&p->tmap, dt, 3, spec, dims, strides, box, estr,
+    CUresult r = get_encoder()(&p->tmap, dt, 4, spec, dims, strides, box, estr,
                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -1189,6 +1198,7 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
         d.ticket = plans[m]->ticket;
         d.scale = runs[m].scale;
         d.tiles = d.S_pad / p->KT;
+        d.cap_tiles = (int)(p->cap / p->KT);
         d.box_bytes = (uint32_t)p->box_rows * kRowBytes;
         d.unit_base = units;
         for (int pr = 0; pr < p->npairs; ++pr)

@@ -67,6 +67,17 @@ struct corr_s {
     cudaEvent_t stage_full[kHostStages] = {};
     int64_t stage_frames = 0;
     int stage_next = 0;
+    // F-engine launches of consecutive pushes alternate between two side
+    // streams, so one launch's last CTAs run beside the next one's first.
+    // The handle's stream waits for them (join_fengines) before anything
+    // that reads the workspace or changes what the F-engine reads.
+    cudaStream_t f_stream[2] = {};
+    cudaEvent_t f_done[2] = {};
+    cudaEvent_t f_fork = nullptr;
+    bool f_pending[2] = {false, false};
+    int f_next = 0;
+    cudaStream_t f_last = nullptr;   // stream of the latest F-engine launch
+    cudaEvent_t f_span = nullptr;    // profiling: start of the open run of side launches
     // coarse integer sample delays (corr_set_sample_delays)
     bool sdelay_on = false;
     int* sdelay = nullptr;          // [N] samples, device
@@ -211,6 +222,36 @@ void prof_end(corr_t h, int cls) {
     h->prof_launches[cls] += 1;
 }
 
+// Make the handle's stream wait for the F-engine launches on the side
+// streams.  With profiling on, the run of side launches since the last join
+// is timed as one span on the handle's stream (launches overlap, so the
+// average launch duration is the span over the launch count).
+int join_fengines(corr_t h) {
+    for (int j = 0; j < 2; ++j)
+        if (h->f_pending[j]) {
+            CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->f_done[j], 0));
+            h->f_pending[j] = false;
+        }
+    if (h->f_span) {
+        cudaEvent_t e = prof_event(h);
+        if (e) {
+            cudaEventRecord(e, h->stream);
+            h->ev_pending[CORR_KERNEL_FENGINE].emplace_back(h->f_span, e);
+        } else {
+            h->ev_pool.push_back(h->f_span);
+        }
+        h->f_span = nullptr;
+    }
+    return CORR_OK;
+}
+
+// Wait on the host for the side streams (before freeing what they read).
+int sync_fengines(corr_t h) {
+    for (int j = 0; j < 2; ++j)
+        if (h->f_stream[j]) CUDA_TRY(h, cudaStreamSynchronize(h->f_stream[j]));
+    return join_fengines(h);
+}
+
 bool narrow(corr_t h) { return h->spec_type == SPEC_F16 || h->spec_type == SPEC_F8; }
 
 // First scales of a narrow-type handle: transform a short prefix of the
@@ -223,6 +264,8 @@ int estimate_scales(corr_t h, const uint8_t* din, int64_t S) {
     const int64_t fit = (int64_t)(ws / ((size_t)h->N * h->C * sizeof(float2)));
     if (S_est > fit) S_est = fit;
     if (S_est < 1) return set_err(h, CORR_EINVAL, "chunk too small to estimate scales");
+    int jrc = join_fengines(h);
+    if (jrc != CORR_OK) return jrc;
     FengineArgs fa{};
     fa.in = din;
     fa.N = h->N;
@@ -244,8 +287,9 @@ int64_t pad_frames(int64_t S) { return (S + kSpecPad - 1) / kSpecPad * kSpecPad;
 
 // F-engine of S frames at `din` (device) into the workspace from frame `off`;
 // raw = true skips the per-antenna corrections (the uncorrected visibilities
-// corr_grad needs).
-int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off = 0) {
+// corr_grad needs).  side = true queues it on the next side stream after the
+// work already on the handle's stream.
+int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off, bool side) {
     const int64_t S_pad = pad_frames(S);
     if (narrow(h) && !h->scales_ready) {
         int rc = estimate_scales(h, din, S);
@@ -265,9 +309,27 @@ int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off 
     fa.spec_type = h->spec_type;
     fa.scale = (h->spec_type == SPEC_F16 || h->spec_type == SPEC_F8) ? h->scale : nullptr;
     fa.debug_out = nullptr;
-    prof_begin(h);
-    CUDA_TRY(h, launch_fengine(fa, h->stream));
-    prof_end(h, CORR_KERNEL_FENGINE);
+    if (!side) {
+        prof_begin(h);
+        CUDA_TRY(h, launch_fengine(fa, h->stream));
+        prof_end(h, CORR_KERNEL_FENGINE);
+        h->f_last = h->stream;
+        return CORR_OK;
+    }
+    const int j = h->f_next;
+    cudaStream_t st = h->f_stream[j];
+    if (h->prof_on && !h->f_span) {
+        h->f_span = prof_event(h);
+        if (h->f_span) cudaEventRecord(h->f_span, h->stream);
+    }
+    CUDA_TRY(h, cudaEventRecord(h->f_fork, h->stream));
+    CUDA_TRY(h, cudaStreamWaitEvent(st, h->f_fork, 0));
+    CUDA_TRY(h, launch_fengine(fa, st));
+    CUDA_TRY(h, cudaEventRecord(h->f_done[j], st));
+    h->f_pending[j] = true;
+    h->f_next = j ^ 1;
+    h->f_last = st;
+    if (h->f_span) h->prof_launches[CORR_KERNEL_FENGINE] += 1;
     return CORR_OK;
 }
 
@@ -321,6 +383,8 @@ int xengine_pass(corr_t h, int64_t S_pad, double2* acc) {
 
 // X-engine over the frames waiting in the workspace.
 int flush(corr_t h) {
+    int jrc = join_fengines(h);
+    if (jrc != CORR_OK) return jrc;
     if (h->fill == 0) return CORR_OK;
     const int64_t f = h->fill;
     h->fill = 0;
@@ -341,7 +405,9 @@ int stage_frames(corr_t h, const uint8_t* din, int64_t S, bool raw, double2* acc
         if (rc != CORR_OK) return rc;
     }
     h->fill_acc = acc;
-    int rc = fengine_pass(h, din, S, raw, h->fill);
+    // with sample delays every chunk goes through the one `shifted` buffer,
+    // so their F-engine launches stay on the handle's stream
+    int rc = fengine_pass(h, din, S, raw, h->fill, !h->sdelay_on);
     if (rc != CORR_OK) return rc;
     const bool whole = S % kSpecPad == 0;
     h->fill += whole ? S : pad_frames(S);
@@ -406,7 +472,7 @@ int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, doubl
         }
         int rc = stage_frames(h, din, S, raw, acc);
         if (rc != CORR_OK) return rc;
-        if (host) CUDA_TRY(h, cudaEventRecord(h->stage_free[b], h->stream));
+        if (host) CUDA_TRY(h, cudaEventRecord(h->stage_free[b], h->f_last));
         f0 += S;
     }
     return CORR_OK;
@@ -414,6 +480,8 @@ int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, doubl
 
 void destroy_impl(corr_t h) {
     if (!h) return;
+    for (int j = 0; j < 2; ++j)
+        if (h->f_stream[j]) cudaStreamSynchronize(h->f_stream[j]);
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
     free_workspace(h);
@@ -443,6 +511,12 @@ void destroy_impl(corr_t h) {
             cudaEventDestroy(pr.second);
         }
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->f_span) cudaEventDestroy(h->f_span);
+    for (int j = 0; j < 2; ++j) {
+        if (h->f_done[j]) cudaEventDestroy(h->f_done[j]);
+        if (h->f_stream[j]) cudaStreamDestroy(h->f_stream[j]);
+    }
+    if (h->f_fork) cudaEventDestroy(h->f_fork);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     delete h;
@@ -490,6 +564,13 @@ int corr_create(corr_t* out, int N, int K, int dtype) {
     h->own_stream = true;
     if (cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(set_err(h, CORR_ECUDA, "stream creation failed"));
+    for (int j = 0; j < 2; ++j)
+        if (cudaStreamCreateWithFlags(&h->f_stream[j], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->f_done[j], cudaEventDisableTiming) != cudaSuccess)
+            return bail(set_err(h, CORR_ECUDA, "stream creation failed"));
+    if (cudaEventCreateWithFlags(&h->f_fork, cudaEventDisableTiming) != cudaSuccess)
+        return bail(set_err(h, CORR_ECUDA, "event creation failed"));
+    h->f_last = h->stream;
 
     if (h->use_tc) {
         int rc = tc_plan_create(&h->tc, N, h->C, h->spec_type, h->err);
@@ -548,6 +629,8 @@ int corr_create(corr_t* out, int N, int K, int dtype) {
 
 int corr_set_stream(corr_t h, void* stream) {
     if (!h) return CORR_EINVAL;
+    int jrc = join_fengines(h);
+    if (jrc != CORR_OK) return jrc;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     if (h->own_stream) {
         cudaStreamDestroy(h->stream);
@@ -564,6 +647,8 @@ int corr_set_chunk(corr_t h, int64_t max_spectra) {
                        (long long)max_spectra);
     if (h->n_spec != 0)
         return set_err(h, CORR_ESTATE, "chunk size can only change between integrations");
+    int jrc = sync_fengines(h);
+    if (jrc != CORR_OK) return jrc;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return alloc_workspace(h, max_spectra);
 }
@@ -698,6 +783,9 @@ int corr_test_fault(corr_t h, int kind, double wait_limit_s) {
     if (!h) return CORR_EINVAL;
     if (kind != 1) return set_err(h, CORR_EINVAL, "unknown fault kind %d", kind);
     if (!h->use_tc) return set_err(h, CORR_EINVAL, "the withheld-copy fault needs a tensor-core handle");
+    int jrc = sync_fengines(h);
+    if (jrc != CORR_OK) return jrc;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return tc_test_withhold(h->tc, wait_limit_s, h->err);
 }
 
@@ -722,6 +810,9 @@ int corr_set_sample_delays(corr_t h, const int32_t* delays) {
 
 int corr_set_corrections(corr_t h, const float* gains, const float* delays) {
     if (!h) return CORR_EINVAL;
+    // launches already queued keep the old table
+    int jrc = join_fengines(h);
+    if (jrc != CORR_OK) return jrc;
     if (!gains && !delays) {
         h->corr_on = false;
         return CORR_OK;
@@ -912,6 +1003,8 @@ int corr_get_scales(corr_t h, float* scales) {
 
 int corr_profile_enable(corr_t h, int on) {
     if (!h) return CORR_EINVAL;
+    int jrc = join_fengines(h);          // closes an open span of side launches
+    if (jrc != CORR_OK) return jrc;
     h->prof_on = on != 0;
     return CORR_OK;
 }
@@ -919,6 +1012,8 @@ int corr_profile_enable(corr_t h, int on) {
 int corr_profile_read(corr_t h, int64_t* launches, double* ms, int n) {
     if (!h) return CORR_EINVAL;
     if (n < 0) return set_err(h, CORR_EINVAL, "n < 0");
+    int jrc = join_fengines(h);
+    if (jrc != CORR_OK) return jrc;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     for (int c = 0; c < CORR_KERNEL_COUNT; ++c) {
         for (auto& pr : h->ev_pending[c]) {
@@ -1033,7 +1128,7 @@ int batch_enqueue(corr_batch_t b, const uint8_t* const* samples, const int64_t* 
             if (f0 >= frames[m]) continue;
             const int64_t S = std::min(h->cap, frames[m] - f0);
             const int64_t rec = (int64_t)h->N * (h->K / 2);
-            int rc = fengine_pass(h, samples[m] + f0 * rec, S, false);
+            int rc = fengine_pass(h, samples[m] + f0 * rec, S, false, 0, true);
             if (rc != CORR_OK) return batch_from_handle(b, m, rc);
             TcRun r{};
             r.S_pad = pad_frames(S);
@@ -1044,6 +1139,11 @@ int batch_enqueue(corr_batch_t b, const uint8_t* const* samples, const int64_t* 
             plans[na] = h->tc;
             runs[na] = r;
             idx[na++] = m;
+        }
+        // the modes' F-engines run side by side; the launch waits for all
+        for (int a = 0; a < na; ++a) {
+            int rc = join_fengines(b->h[idx[a]]);
+            if (rc != CORR_OK) return batch_from_handle(b, idx[a], rc);
         }
         corr_t h0 = b->h[idx[0]];
         prof_begin(h0);

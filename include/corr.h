@@ -41,7 +41,11 @@
  *  owns its workspaces.  Work is queued on the handle's stream (its own
  *  non-blocking stream unless corr_set_stream gave another).  corr_push
  *  returns once its work is queued; a device input buffer must stay valid
- *  until the next corr_dump or corr_sync.  Every call returns CORR_OK or a
+ *  and unchanged until the next corr_dump or corr_sync.  (The F-engine
+ *  launches of consecutive pushes alternate between two internal streams,
+ *  each starting after the work queued on the handle's stream before its
+ *  push; the handle's stream waits for them before the X-engine, a dump or
+ *  any call that changes what they read.)  Every call returns CORR_OK or a
  *  negative corr_status; on error the accumulated state is unchanged unless
  *  stated, and corr_last_error(h) returns a one-line message (for errors of
  *  corr_create, call corr_last_error(NULL) on the same thread).  One handle

@@ -221,10 +221,17 @@ __device__ __forceinline__ float nib_hi(unsigned b) {
 }
 
 constexpr int kOutDebug = -1;
-constexpr int kStgRow = 513;        // staging row stride (floats): [frame][plane*256 + k]
-// staging floats, rounded up to a multiple of 4 so the exchange area after it
-// stays 16-byte aligned (its first use is a 16-byte store)
-constexpr int kStgFloats = (kF512Frames * kStgRow + 3) & ~3;
+// Staging row stride (floats): [frame][plane*256 + k].  547 = 3 mod 32 keeps
+// both the staging writes and the store phase's column reads on distinct
+// banks, and leaves room in a row for one group's exchange area (16 x 17
+// complex = 544 floats) at the 16-byte aligned offset f mod 4 within row f.
+// A group exchanges through the row of its second frame: during the first
+// round no group writes that row, and in the second the group itself writes
+// it only after its exchange.  No other shared memory is needed, so three
+// CTAs fit on an SM.
+constexpr int kStgRow = 547;
+constexpr int kStgFloats = kF512Frames * kStgRow;
+static_assert(kStgRow % 32 == 3 && kStgRow >= 16 * kXStride * 2 + 3, "staging row layout");
 
 // Four consecutive frames of one workspace row (channel k, row r) from the
 // staging buffer, converted and stored with one vector store per plane.
@@ -261,12 +268,11 @@ __device__ __forceinline__ void store4(void* spec, int64_t off, int64_t plane_st
 }
 
 template <int OUT>
-__global__ void __launch_bounds__(kF512Threads, 2) fengine_k512(FengineArgs a) {
+__global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
     constexpr bool DEBUG = OUT == kOutDebug;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* stg = reinterpret_cast<float*>(smem_raw);                        // [32][513]
-    float2* xch = reinterpret_cast<float2*>(stg + (DEBUG ? 0 : kStgFloats));  // [16][16*17]
-    float2* tw_stage = xch + 16 * 16 * kXStride;                            // [16 k1][16 t]
+    float* stg = reinterpret_cast<float*>(smem_raw);                        // [32][547]
+    float2* tw_stage = reinterpret_cast<float2*>(stg + kStgFloats);         // [16 k1][16 t]
     float2* tw_post = tw_stage + 256;                                       // [256]
 
     const int tid = threadIdx.x;
@@ -299,7 +305,8 @@ __global__ void __launch_bounds__(kF512Threads, 2) fengine_k512(FengineArgs a) {
     }
     __syncthreads();
 
-    float2* gx = xch + grp * 16 * kXStride;
+    const int fx = warp + 8 + 16 * half;             // the group's second frame
+    float2* gx = reinterpret_cast<float2*>(stg + fx * kStgRow + (fx & 3));
     unsigned char* gbytes = reinterpret_cast<unsigned char*>(gx);
 
 #pragma unroll 1
@@ -329,19 +336,14 @@ __global__ void __launch_bounds__(kF512Threads, 2) fengine_k512(FengineArgs a) {
         dft16(x);
         // x[q] = Z[lane + 16 q]; real-to-complex split with the partner Z[256 - k]
         const int src = (16 - lane) & 15;
-        float2 z[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            float2 pz;
-            pz.x = __shfl_sync(0xffffffffu, x[15 - q].x, src, 16);
-            pz.y = __shfl_sync(0xffffffffu, x[15 - q].y, src, 16);
-            if (lane == 0) pz = x[(16 - q) & 15];
-            z[q] = pz;
-        }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int k = lane + 16 * q;
-            const float2 zk = x[q], zc = z[q];
+            float2 zc;
+            zc.x = __shfl_sync(0xffffffffu, x[15 - q].x, src, 16);
+            zc.y = __shfl_sync(0xffffffffu, x[15 - q].y, src, 16);
+            if (lane == 0) zc = x[(16 - q) & 15];
+            const float2 zk = x[q];
             const float2 S = make_float2(zk.x + zc.x, zk.y - zc.y);
             const float2 D = make_float2(zk.x - zc.x, zk.y + zc.y);
             const float2 wd = cmul(tw_post[k], D);
@@ -750,8 +752,9 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
         const int64_t fr = dbg ? a.S : a.S_pad;
         if (fr <= 0) return cudaSuccess;
         dim3 grid((unsigned)((fr + kF512Frames - 1) / kF512Frames), (unsigned)a.N);
-        const size_t tables = (size_t)16 * 16 * kXStride * sizeof(float2) + 512 * sizeof(float2);
-        const size_t smem = dbg ? tables : tables + (size_t)kStgFloats * sizeof(float);
+        // staging (also the exchange areas) and the twiddle tables, for the
+        // debug output too
+        const size_t smem = (size_t)kStgFloats * sizeof(float) + 512 * sizeof(float2);
         auto go = [&](auto kern) -> cudaError_t {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);

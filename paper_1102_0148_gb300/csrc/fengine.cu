@@ -334,20 +334,15 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
         for (int t = 0; t < 16; ++t) x[t] = gx[lane * kXStride + t];
         __syncwarp();
         dft16(x);
-        // x[q] = Z[lane + 16 q]; real-to-complex split with the partner Z[256 - k]
+        // x[q] = Z[lane + 16 q].  Slot q < 8 of lane k1 makes both X[k] and
+        // X[256 - k], k = k1 + 16 q, from Z[k] and its partner Z[256 - k]
+        // (register 15 - q of lane 16 - k1; for lane 0 its own register
+        // 16 - q): with S = Z[k] + conj Z[256-k] and D = Z[k] - conj Z[256-k],
+        // X[k] = c S + w'_k D and, as w'_{256-k} = conj w'_k,
+        // X[256 - k] = conj(c S - w'_k D).  Lane 0's slot 0 makes X[0] and,
+        // in place of the dropped Nyquist term, X[128] = post conj Z[128].
         const int src = (16 - lane) & 15;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int k = lane + 16 * q;
-            float2 zc;
-            zc.x = __shfl_sync(0xffffffffu, x[15 - q].x, src, 16);
-            zc.y = __shfl_sync(0xffffffffu, x[15 - q].y, src, 16);
-            if (lane == 0) zc = x[(16 - q) & 15];
-            const float2 zk = x[q];
-            const float2 S = make_float2(zk.x + zc.x, zk.y - zc.y);
-            const float2 D = make_float2(zk.x - zc.x, zk.y + zc.y);
-            const float2 wd = cmul(tw_post[k], D);
-            float2 X = make_float2(fmaf(chalf, S.x, wd.x), fmaf(chalf, S.y, wd.y));
+        auto emit = [&](int k, float2 X) {
             if (a.corr) X = cmul(__ldg(a.corr + (int64_t)i * 256 + k), X);
             if (DEBUG) {
                 if (s < a.S) a.debug_out[((int64_t)i * a.S + s) * 256 + k] = X;
@@ -360,6 +355,26 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
                 stg[f * kStgRow + k] = X.x;
                 stg[f * kStgRow + 256 + k] = X.y;
             }
+        };
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = lane + 16 * q;
+            float2 zc;
+            zc.x = __shfl_sync(0xffffffffu, x[15 - q].x, src, 16);
+            zc.y = __shfl_sync(0xffffffffu, x[15 - q].y, src, 16);
+            if (lane == 0) zc = x[(16 - q) & 15];
+            const float2 zk = x[q];
+            const float2 S = make_float2(zk.x + zc.x, zk.y - zc.y);
+            const float2 D = make_float2(zk.x - zc.x, zk.y + zc.y);
+            const float2 B = cmul(tw_post[k], D);
+            emit(k, make_float2(fmaf(chalf, S.x, B.x), fmaf(chalf, S.y, B.y)));
+            float2 Xp = make_float2(fmaf(chalf, S.x, -B.x), -fmaf(chalf, S.y, -B.y));
+            int kp = 256 - k;
+            if (q == 0 && lane == 0) {
+                Xp = make_float2(post * x[8].x, -post * x[8].y);
+                kp = 128;
+            }
+            emit(kp, Xp);
         }
     }
     if (DEBUG) return;

@@ -220,6 +220,36 @@ __device__ __forceinline__ float nib_hi(unsigned b) {
     return fmaf(__int_as_float((int)((b & 0xF0u) ^ 0x4B000080u)), 0.0625f, -524296.0f);
 }
 
+// cos(q pi / 16) and sin(q pi / 16) for q in [0, 16].
+__device__ __forceinline__ float cos_pi16(int q) {
+    float r = 0.0f;
+    switch (q < 9 ? q : 16 - q) {
+        case 0: r = 1.0f; break;
+        case 1: r = 0.980785280403230449f; break;
+        case 2: r = 0.923879532511286756f; break;
+        case 3: r = 0.831469612302545237f; break;
+        case 4: r = 0.707106781186547524f; break;
+        case 5: r = 0.555570233019602225f; break;
+        case 6: r = 0.382683432365089772f; break;
+        case 7: r = 0.195090322016128268f; break;
+        default: r = 0.0f; break;
+    }
+    return q < 9 ? r : -r;
+}
+__device__ __forceinline__ float sin_pi16(int q) { return cos_pi16(q < 8 ? 8 - q : q - 8); }
+
+// W32^q d = exp(-2 pi i q / 32) d for a compile-time q in [0, 16).
+__device__ __forceinline__ float2 w32mul(float2 d, int q) {
+    if (q == 0) return d;
+    if (q == 8) return make_float2(d.y, -d.x);
+    if (q == 4) {
+        constexpr float r2 = 0.707106781186547524f;
+        return make_float2(r2 * (d.x + d.y), r2 * (d.y - d.x));
+    }
+    const float c = cos_pi16(q), s = sin_pi16(q);
+    return make_float2(fmaf(c, d.x, s * d.y), fmaf(c, d.y, -s * d.x));
+}
+
 constexpr int kOutDebug = -1;
 // Staging row stride (floats): [frame][plane*256 + k].  547 = 3 mod 32 keeps
 // both the staging writes and the store phase's column reads on distinct
@@ -272,8 +302,7 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
     constexpr bool DEBUG = OUT == kOutDebug;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* stg = reinterpret_cast<float*>(smem_raw);                        // [32][547]
-    float2* tw_stage = reinterpret_cast<float2*>(stg + kStgFloats);         // [16 k1][16 t]
-    float2* tw_post = tw_stage + 256;                                       // [256]
+    float2* tw_base = reinterpret_cast<float2*>(stg + kStgFloats);          // [2][4 m][16 t]
 
     const int tid = threadIdx.x;
     const int lane = tid & 15;
@@ -286,15 +315,18 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
     // real-split constants: X = c (zk + conj zc) + w'_k (zk - conj zc) with
     // c = 1/2 and w'_k = W512^k / (2i), both times the pre-scale.
     const float post = OUT == SPEC_F16X2 ? kSplitScale : 1.0f;
-
-    // twiddle tables: W256^{t k1} = W512^{2 t k1} and w'_k
-    {
-        const int k1 = tid >> 4, t = tid & 15;
-        tw_stage[tid] = a.twiddle[2 * t * k1];
-        const float2 w = a.twiddle[tid];
-        tw_post[tid] = make_float2(0.5f * post * w.y, -0.5f * post * w.x);
-    }
     const float chalf = 0.5f * post;
+
+    // Twiddles, kept off the shared-memory pipe where arithmetic can stand
+    // in: the stage twiddle W256^{t k1}, k1 = p + 4 r, is W256^{t p} W256^{4 t r}
+    // from a 1 KB table of the six bases, and the split's W512^k, k = t + 16 q,
+    // is W512^t (a register) times W32^q (an immediate).
+    if (tid < 128) {
+        const int j = tid >> 6, m = (tid >> 4) & 3, t = tid & 15;
+        tw_base[tid] = a.twiddle[2 * t * m * (j ? 4 : 1)];   // W256^{t m 4^j}
+    }
+    const float2 wt = __ldg(a.twiddle + lane);
+    const float2 u = make_float2(chalf * wt.x, chalf * wt.y);   // c W512^t
 
     // prefetch both rounds' 16 bytes per lane
     uint4 raw0 = make_uint4(0u, 0u, 0u, 0u), raw1 = raw0;
@@ -325,8 +357,19 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
         __syncwarp();
         dft16(x);
         // twiddle W256^{t k1}, then exchange: lane k1 collects register k1 of every t
+        {
+            float2 wp[4], wr[4];
 #pragma unroll
-        for (int k1 = 1; k1 < 16; ++k1) x[k1] = cmul(x[k1], tw_stage[k1 * 16 + lane]);
+            for (int m = 1; m < 4; ++m) {
+                wp[m] = tw_base[m * 16 + lane];
+                wr[m] = tw_base[64 + m * 16 + lane];
+            }
+#pragma unroll
+            for (int k1 = 1; k1 < 16; ++k1) {
+                if (k1 & 3) x[k1] = cmul(x[k1], wp[k1 & 3]);
+                if (k1 >> 2) x[k1] = cmul(x[k1], wr[k1 >> 2]);
+            }
+        }
 #pragma unroll
         for (int k1 = 0; k1 < 16; ++k1) gx[k1 * kXStride + lane] = x[k1];
         __syncwarp();
@@ -366,7 +409,9 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
             const float2 zk = x[q];
             const float2 S = make_float2(zk.x + zc.x, zk.y - zc.y);
             const float2 D = make_float2(zk.x - zc.x, zk.y + zc.y);
-            const float2 B = cmul(tw_post[k], D);
+            // B = w'_k D = -i c W512^t W32^q D
+            const float2 v = cmul(u, w32mul(D, q));
+            const float2 B = make_float2(v.y, -v.x);
             emit(k, make_float2(fmaf(chalf, S.x, B.x), fmaf(chalf, S.y, B.y)));
             float2 Xp = make_float2(fmaf(chalf, S.x, -B.x), -fmaf(chalf, S.y, -B.y));
             int kp = 256 - k;
@@ -767,9 +812,9 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
         const int64_t fr = dbg ? a.S : a.S_pad;
         if (fr <= 0) return cudaSuccess;
         dim3 grid((unsigned)((fr + kF512Frames - 1) / kF512Frames), (unsigned)a.N);
-        // staging (also the exchange areas) and the twiddle tables, for the
+        // staging (also the exchange areas) and the twiddle bases, for the
         // debug output too
-        const size_t smem = (size_t)kStgFloats * sizeof(float) + 512 * sizeof(float2);
+        const size_t smem = (size_t)kStgFloats * sizeof(float) + 128 * sizeof(float2);
         auto go = [&](auto kern) -> cudaError_t {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);

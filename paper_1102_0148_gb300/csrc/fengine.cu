@@ -460,18 +460,22 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
 constexpr int kF1024Frames = 16;     // frames per CTA, two per warp
 constexpr int kF1024Threads = 256;
 constexpr int kX1024Stride = 33;     // exchange row stride (complex)
-constexpr int kStg1024Row = 1026;    // staging row stride (floats), conflict-free reads
+// Staging row stride (floats): 1058 = 2 mod 8 keeps the store phase's column
+// reads on distinct banks, and a row holds one warp's exchange area (16 x 33
+// complex = 1056 floats) at the 16-byte aligned offset 2 (f mod 2).  A warp
+// exchanges through the row of its second frame, as in the K = 512 kernel,
+// so three CTAs fit on an SM.
+constexpr int kStg1024Row = 1058;
 constexpr int kStg1024Floats = kF1024Frames * kStg1024Row;
+static_assert(kStg1024Row % 8 == 2 && kStg1024Row >= 16 * kX1024Stride * 2 + 2, "staging row layout");
 
 template <int OUT>
-__global__ void __launch_bounds__(kF1024Threads, 2) fengine_k1024(FengineArgs a) {
+__global__ void __launch_bounds__(kF1024Threads, 3) fengine_k1024(FengineArgs a) {
     constexpr bool DEBUG = OUT == kOutDebug;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* stg = reinterpret_cast<float*>(smem_raw);                        // [16][1026]
-    float2* xch = reinterpret_cast<float2*>(stg + (DEBUG ? 0 : kStg1024Floats));  // [8][16][33]
-    float2* tw_stage = xch + 8 * 16 * kX1024Stride;                         // [16 k1][32 t]
-    float2* tw_post = tw_stage + 512;                                       // [512]
-    float2* tw32 = tw_post + 512;                                           // [2][16]
+    float* stg = reinterpret_cast<float*>(smem_raw);                        // [16][1058]
+    float2* tw_base = reinterpret_cast<float2*>(stg + kStg1024Floats);      // [2][4 m][32 t]
+    float2* tw32 = tw_base + 256;                                           // [2][16]
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -481,15 +485,18 @@ __global__ void __launch_bounds__(kF1024Threads, 2) fengine_k1024(FengineArgs a)
     const int i = blockIdx.y;
     const int64_t s0 = (int64_t)blockIdx.x * kF1024Frames;
     const float post = OUT == SPEC_F16X2 ? kSplitScale : 1.0f;
-    for (int e = tid; e < 512; e += kF1024Threads) {
-        const int kk = e >> 5, t = e & 31;
-        tw_stage[e] = a.twiddle[2 * t * kk];               // W512^{t k1} = W1024^{2 t k1}
-        const float2 w = a.twiddle[e];
-        tw_post[e] = make_float2(0.5f * post * w.y, -0.5f * post * w.x);
+    const float chalf = 0.5f * post;
+    // Twiddles as in the K = 512 kernel: the stage twiddle W512^{t q},
+    // q = p + 4 r, is W512^{t p} W512^{4 t r} from a table of the six bases,
+    // and the split's W1024^k, k = l + 32 q, is W1024^l W32^q.
+    {
+        const int j = tid >> 7, m = (tid >> 5) & 3, t = tid & 31;
+        tw_base[tid] = a.twiddle[2 * t * m * (j ? 4 : 1)];   // W512^{t m 4^j}
     }
     // [2][16]: ones, then W32^{t'} = W1024^{32 t'}
     if (tid < 32) tw32[tid] = tid < 16 ? make_float2(1.0f, 0.0f) : a.twiddle[32 * (tid - 16)];
-    const float chalf = 0.5f * post;
+    const float2 wl = __ldg(a.twiddle + lane);
+    const float2 u = make_float2(chalf * wl.x, chalf * wl.y);   // c W1024^l
 
     uint4 raw0 = make_uint4(0u, 0u, 0u, 0u), raw1 = raw0;
     {
@@ -499,7 +506,8 @@ __global__ void __launch_bounds__(kF1024Threads, 2) fengine_k1024(FengineArgs a)
     }
     __syncthreads();
 
-    float2* gx = xch + warp * 16 * kX1024Stride;
+    const int fx = warp + 8;                         // the warp's second frame
+    float2* gx = reinterpret_cast<float2*>(stg + fx * kStg1024Row + 2 * (fx & 1));
     unsigned char* gbytes = reinterpret_cast<unsigned char*>(gx);
 
 #pragma unroll 1
@@ -516,8 +524,19 @@ __global__ void __launch_bounds__(kF1024Threads, 2) fengine_k1024(FengineArgs a)
         }
         __syncwarp();
         dft16(x);
+        {
+            float2 wp[4], wr[4];
 #pragma unroll
-        for (int q = 1; q < 16; ++q) x[q] = cmul(x[q], tw_stage[q * 32 + lane]);
+            for (int m = 1; m < 4; ++m) {
+                wp[m] = tw_base[m * 32 + lane];
+                wr[m] = tw_base[128 + m * 32 + lane];
+            }
+#pragma unroll
+            for (int q = 1; q < 16; ++q) {
+                if (q & 3) x[q] = cmul(x[q], wp[q & 3]);
+                if (q >> 2) x[q] = cmul(x[q], wr[q >> 2]);
+            }
+        }
 #pragma unroll
         for (int q = 0; q < 16; ++q) gx[q * kX1024Stride + lane] = x[q];
         __syncwarp();
@@ -538,26 +557,13 @@ __global__ void __launch_bounds__(kF1024Threads, 2) fengine_k1024(FengineArgs a)
             x[t] = t > 0 ? cmul(v, twh[t]) : v;
         }
         dft16(x);
-        // x[q] = Z[k1 + 16 hh + 32 q]; partner Z[512 - k]
-        const int src = ((16 - k1) & 15) + 16 * (1 - hh);
-        float2 z[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            float2 pz;
-            pz.x = __shfl_sync(0xffffffffu, x[15 - q].x, src);
-            pz.y = __shfl_sync(0xffffffffu, x[15 - q].y, src);
-            if (lane == 0) pz = x[(16 - q) & 15];
-            if (lane == 16) pz = x[15 - q];
-            z[q] = pz;
-        }
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int k = k1 + 16 * hh + 32 * q;
-            const float2 zk = x[q], zc = z[q];
-            const float2 S = make_float2(zk.x + zc.x, zk.y - zc.y);
-            const float2 D = make_float2(zk.x - zc.x, zk.y + zc.y);
-            const float2 wd = cmul(tw_post[k], D);
-            float2 X = make_float2(fmaf(chalf, S.x, wd.x), fmaf(chalf, S.y, wd.y));
+        // x[q] = Z[l + 32 q], l = k1 + 16 hh.  As in the K = 512 kernel, slot
+        // q < 8 makes X[k] and X[512 - k] for k = l + 32 q from Z[k] and its
+        // partner Z[512 - k], register 15 - q of lane 32 - l (lane 16 is its
+        // own partner; lane 0 pairs its own registers q and 16 - q, and its
+        // slot 0 makes X[0] and X[256]).
+        const int src = (32 - lane) & 31;
+        auto emit = [&](int k, float2 X) {
             if (a.corr) X = cmul(__ldg(a.corr + (int64_t)i * 512 + k), X);
             if (DEBUG) {
                 if (s < a.S) a.debug_out[((int64_t)i * a.S + s) * 512 + k] = X;
@@ -570,6 +576,28 @@ __global__ void __launch_bounds__(kF1024Threads, 2) fengine_k1024(FengineArgs a)
                 stg[f * kStg1024Row + k] = X.x;
                 stg[f * kStg1024Row + 512 + k] = X.y;
             }
+        };
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = lane + 32 * q;
+            float2 zc;
+            zc.x = __shfl_sync(0xffffffffu, x[15 - q].x, src);
+            zc.y = __shfl_sync(0xffffffffu, x[15 - q].y, src);
+            if (lane == 0) zc = x[(16 - q) & 15];
+            const float2 zk = x[q];
+            const float2 S = make_float2(zk.x + zc.x, zk.y - zc.y);
+            const float2 D = make_float2(zk.x - zc.x, zk.y + zc.y);
+            // B = w'_k D = -i c W1024^l W32^q D
+            const float2 v = cmul(u, w32mul(D, q));
+            const float2 B = make_float2(v.y, -v.x);
+            emit(k, make_float2(fmaf(chalf, S.x, B.x), fmaf(chalf, S.y, B.y)));
+            float2 Xp = make_float2(fmaf(chalf, S.x, -B.x), -fmaf(chalf, S.y, -B.y));
+            int kp = 512 - k;
+            if (q == 0 && lane == 0) {
+                Xp = make_float2(post * x[8].x, -post * x[8].y);
+                kp = 256;
+            }
+            emit(kp, Xp);
         }
     }
     if (DEBUG) return;
@@ -834,8 +862,9 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
         const int64_t fr = dbg ? a.S : a.S_pad;
         if (fr <= 0) return cudaSuccess;
         dim3 grid((unsigned)((fr + kF1024Frames - 1) / kF1024Frames), (unsigned)a.N);
-        const size_t tables = ((size_t)8 * 16 * kX1024Stride + 512 + 512 + 32) * sizeof(float2);
-        const size_t smem = dbg ? tables : tables + (size_t)kStg1024Floats * sizeof(float);
+        // staging (also the exchange areas) and the twiddle tables, for the
+        // debug output too
+        const size_t smem = (size_t)kStg1024Floats * sizeof(float) + (256 + 32) * sizeof(float2);
         auto go = [&](auto kern) -> cudaError_t {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);

@@ -84,7 +84,11 @@ struct corr_s {
     std::vector<int> sdelay_host;   // the same, for checkpoints
     uint8_t* hist[2] = {};          // [N][K/2] last frame of the stream so far (ping-pong)
     int hist_cur = 0;
-    uint8_t* shifted = nullptr;     // [cap][N][K/2] delayed chunk
+    // delayed chunks, alternately: [cap][N][K/2] each; shift_free[b] follows
+    // the F-engine launch that last read buffer b
+    uint8_t* shifted[2] = {};
+    cudaEvent_t shift_free[2] = {};
+    int shift_cur = 0;
     int64_t shifted_frames = 0;
     void* vis_dev = nullptr;
     int64_t n_spec = 0;
@@ -405,13 +409,33 @@ int stage_frames(corr_t h, const uint8_t* din, int64_t S, bool raw, double2* acc
         if (rc != CORR_OK) return rc;
     }
     h->fill_acc = acc;
-    // with sample delays every chunk goes through the one `shifted` buffer,
-    // so their F-engine launches stay on the handle's stream
-    int rc = fengine_pass(h, din, S, raw, h->fill, !h->sdelay_on);
+    int rc = fengine_pass(h, din, S, raw, h->fill, true);
     if (rc != CORR_OK) return rc;
     const bool whole = S % kSpecPad == 0;
     h->fill += whole ? S : pad_frames(S);
     if (!whole || h->fill >= h->cap) return flush(h);
+    return CORR_OK;
+}
+
+// Two delayed-chunk buffers of `cap` frames each (the F-engine of one chunk
+// may still read its buffer while the next chunk is delayed into the other).
+int alloc_shifted(corr_t h) {
+    if (h->shifted_frames >= h->cap) return CORR_OK;
+    int rc = sync_fengines(h);              // queued launches may read the old buffers
+    if (rc != CORR_OK) return rc;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    const size_t bytes = (size_t)h->cap * h->N * (h->K / 2);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(h->shifted[b]);
+        h->shifted[b] = nullptr;
+    }
+    h->shifted_frames = 0;
+    for (int b = 0; b < 2; ++b) {
+        CUDA_TRY(h, cudaMalloc((void**)&h->shifted[b], bytes));
+        if (!h->shift_free[b])
+            CUDA_TRY(h, cudaEventCreateWithFlags(&h->shift_free[b], cudaEventDisableTiming));
+    }
+    h->shifted_frames = h->cap;
     return CORR_OK;
 }
 
@@ -433,12 +457,9 @@ int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, doubl
             CUDA_TRY(h, cudaEventCreateWithFlags(&h->stage_full[b], cudaEventDisableTiming));
         }
     }
-    if (h->sdelay_on && h->shifted_frames < h->cap) {      // the pass grew since
-        cudaFree(h->shifted);
-        h->shifted = nullptr;
-        h->shifted_frames = 0;
-        CUDA_TRY(h, cudaMalloc((void**)&h->shifted, (size_t)h->cap * rec));
-        h->shifted_frames = h->cap;
+    if (h->sdelay_on) {                         // the pass may have grown since
+        int rc = alloc_shifted(h);
+        if (rc != CORR_OK) return rc;
     }
     for (int64_t f0 = 0; f0 < frames;) {
         if (h->fill > 0 && acc != h->fill_acc) {
@@ -460,18 +481,23 @@ int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, doubl
             CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->stage_full[b], 0));
             din = h->stage[b];
         }
+        int sb = -1;
         if (h->sdelay_on) {
             // the stream's history feeds pushes only; corr_grad's samples
             // (raw) start from zeros and leave it untouched
             const uint8_t* hin = raw ? nullptr : h->hist[h->hist_cur];
             uint8_t* hout = raw ? nullptr : h->hist[h->hist_cur ^ 1];
-            CUDA_TRY(h, launch_sample_delay(din, S, h->N, h->K, h->sdelay, hin, hout, h->shifted,
+            sb = h->shift_cur;
+            h->shift_cur ^= 1;
+            CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->shift_free[sb], 0));
+            CUDA_TRY(h, launch_sample_delay(din, S, h->N, h->K, h->sdelay, hin, hout, h->shifted[sb],
                                             h->stream));
             if (!raw) h->hist_cur ^= 1;
-            din = h->shifted;
+            din = h->shifted[sb];
         }
         int rc = stage_frames(h, din, S, raw, acc);
         if (rc != CORR_OK) return rc;
+        if (sb >= 0) CUDA_TRY(h, cudaEventRecord(h->shift_free[sb], h->f_last));
         if (host) CUDA_TRY(h, cudaEventRecord(h->stage_free[b], h->f_last));
         f0 += S;
     }
@@ -498,7 +524,10 @@ void destroy_impl(corr_t h) {
     cudaFree(h->sdelay);
     cudaFree(h->hist[0]);
     cudaFree(h->hist[1]);
-    cudaFree(h->shifted);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(h->shifted[b]);
+        if (h->shift_free[b]) cudaEventDestroy(h->shift_free[b]);
+    }
     for (int b = 0; b < kHostStages; ++b) {
         cudaFree(h->stage[b]);
         if (h->stage_free[b]) cudaEventDestroy(h->stage_free[b]);
@@ -689,13 +718,8 @@ int apply_sample_delays(corr_t h, const int* d) {
         CUDA_TRY(h, cudaMalloc((void**)&h->sdelay, h->N * sizeof(int)));
         for (int b = 0; b < 2; ++b) CUDA_TRY(h, cudaMalloc((void**)&h->hist[b], hb));
     }
-    if (h->shifted_frames < h->cap) {
-        cudaFree(h->shifted);
-        h->shifted = nullptr;
-        h->shifted_frames = 0;
-        CUDA_TRY(h, cudaMalloc((void**)&h->shifted, (size_t)h->cap * hb));
-        h->shifted_frames = h->cap;
-    }
+    int arc = alloc_shifted(h);
+    if (arc != CORR_OK) return arc;
     if (!h->sdelay_on) {
         CUDA_TRY(h, cudaMemsetAsync(h->hist[h->hist_cur], 0, hb, h->stream));
     }

@@ -80,6 +80,22 @@ def env_rank():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def max_over_ranks(dist, seconds, device):
+    """The slowest rank's time (every rank gets it); `dist` None = one rank."""
+    if dist is None:
+        return seconds
+    import torch
+    tt = torch.tensor([seconds], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(world, units_per_rank, seconds):
+    """Units all ranks processed (replicas: each rank the same amount) per
+    second of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 # ----------------------------------------------------------------------------
 # clocks during the timed region
 # ----------------------------------------------------------------------------
@@ -307,19 +323,14 @@ def main():
     sampler.stop()
     if dist:
         dist.barrier()
-    t = ev0.elapsed_time(ev1) / 1e3
-    if dist:
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(dist, ev0.elapsed_time(ev1) / 1e3, "cuda")
     clocks = sampler.result()
     prof = corr.corr_profile_read(h)
     corr.corr_profile_enable(h, False)
     # every step launches the same kernels
     launches = sum(v[0] for v in prof.values()) * args.steps // max(1, profiled)
 
-    samples_total = world * N_ANT * frames * K_FFT * args.steps
-    value = samples_total / t
+    value = whole_job_rate(world, N_ANT * frames * K_FFT * args.steps, t)
 
     # roofline of the dominant kernel (largest summed event time)
     spec_total = frames * profiled
@@ -381,12 +392,9 @@ def main():
         for _ in range(args.e2e_steps):
             step_host()
         corr.corr_sync(h)                   # the last step's visibilities are in host memory
-        te = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([te], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": world * N_ANT * frames * K_FFT * args.e2e_steps / te, "unit": UNIT,
+        te = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
+        e2e = {"value": whole_job_rate(world, N_ANT * frames * K_FFT * args.e2e_steps, te),
+               "unit": UNIT,
                "h2d_bytes_per_step": frames * rec,
                "d2h_bytes_per_step": host_vis.numel() * host_vis.element_size(),
                "steps": args.e2e_steps, "dump": "corr_dump_async into pinned host memory"}

@@ -117,17 +117,18 @@ __global__ void reduce_partials_kernel(const float2* part, int n_split, int64_t 
 }
 
 // acc [C][P] -> vis [P][C] through 32 x 32 shared-memory tiles, so both the
-// reads (along p) and the writes (along k) are coalesced; acc is cleared.
+// reads (along p) and the writes (along k) are coalesced.  (acc is cleared by
+// a memset after it: zero stores here, to the lines just loaded, held the
+// kernel to a quarter of the HBM bandwidth.)
 constexpr int kDT = 32;
 
-__global__ void __launch_bounds__(kDT * 8) dump_kernel(double2* __restrict__ acc, int C, int P,
-                                                     void* __restrict__ vis, int fp64) {
+__global__ void __launch_bounds__(kDT * 8) dump_kernel(const double2* __restrict__ acc, int C,
+                                                     int P, void* __restrict__ vis, int fp64) {
     __shared__ double2 tile[kDT][kDT + 1];
     const int p0 = blockIdx.x * kDT;
     const int k0 = blockIdx.y * kDT;
     const int tx = threadIdx.x & (kDT - 1);
     const int ty = threadIdx.x / kDT;               // 0..7
-    // all four loads in flight before the clearing stores
     double2 v[kDT / 8];
     const int p = p0 + tx;
 #pragma unroll
@@ -136,11 +137,7 @@ __global__ void __launch_bounds__(kDT * 8) dump_kernel(double2* __restrict__ acc
         v[q] = (k < C && p < P) ? acc[(int64_t)k * P + p] : make_double2(0.0, 0.0);
     }
 #pragma unroll
-    for (int q = 0; q < kDT / 8; ++q) {
-        const int k = k0 + ty + 8 * q;
-        if (k < C && p < P) acc[(int64_t)k * P + p] = make_double2(0.0, 0.0);
-        tile[ty + 8 * q][tx] = v[q];
-    }
+    for (int q = 0; q < kDT / 8; ++q) tile[ty + 8 * q][tx] = v[q];
     __syncthreads();
     const int k = k0 + tx;
 #pragma unroll
@@ -187,7 +184,9 @@ cudaError_t launch_reduce_partials(const float2* partial, int n_split, int64_t C
 cudaError_t launch_dump(double2* acc, int C, int P, void* vis, int fp64, cudaStream_t st) {
     dim3 grid((unsigned)((P + kDT - 1) / kDT), (unsigned)((C + kDT - 1) / kDT));
     dump_kernel<<<grid, kDT * 8, 0, st>>>(acc, C, P, vis, fp64);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(acc, 0, (size_t)C * P * sizeof(double2), st);
 }
 
 }  // namespace gbcorr

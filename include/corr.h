@@ -236,11 +236,15 @@ enum corr_kernel {
 };
 
 /* Instrumentation (no counterpart in the paper): while enabled, every kernel
- * the handle launches is bracketed by a pair of CUDA events on the stream it
- * is launched on.  corr_profile_read waits for the handle's stream, writes
- * for each class c < n the number of launches (launches[c]) and their summed
- * event-to-event time in milliseconds (ms[c]) since the last read, and
- * clears the counters.  Either output may be NULL. */
+ * the handle launches is bracketed by a pair of CUDA events on the handle's
+ * stream.  The F-engine launches of consecutive pushes overlap on the side
+ * streams, so each run of them (up to the next X-engine pass or other call
+ * that waits for them) is bracketed as a whole: ms[CORR_KERNEL_FENGINE] is
+ * the span of those runs and launches[] still counts every launch.
+ * corr_profile_read waits for the handle's stream, writes for each class
+ * c < n the number of launches (launches[c]) and their summed event-to-event
+ * time in milliseconds (ms[c]) since the last read, and clears the
+ * counters.  Either output may be NULL. */
 int corr_profile_enable(corr_t h, int on);
 int corr_profile_read(corr_t h, int64_t* launches, double* ms, int n);
 

@@ -100,18 +100,33 @@ __global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt) {
         }
 }
 
+// The partials of one workspace pass are summed in FP32 (four independent
+// running sums, so the loads overlap; a pass holds at most 131072 frames), and
+// the pass total is added to the FP64 accumulator.  FP64 arithmetic runs at a
+// small fraction of the FP32 rate on this GPU, so one FP64 add per element
+// and pass keeps the kernel bound by its loads.
 __global__ void reduce_partials_kernel(const float2* part, int n_split, int64_t CP, double2* acc) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < CP;
          e += (int64_t)gridDim.x * blockDim.x) {
-        double re = 0.0, im = 0.0;
-        for (int s = 0; s < n_split; ++s) {
+        float2 t[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
+                       make_float2(0.f, 0.f)};
+        int s = 0;
+        for (; s + 4 <= n_split; s += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 v = part[(int64_t)(s + q) * CP + e];
+                t[q].x += v.x;
+                t[q].y += v.y;
+            }
+        }
+        for (; s < n_split; ++s) {
             const float2 v = part[(int64_t)s * CP + e];
-            re += (double)v.x;
-            im += (double)v.y;
+            t[0].x += v.x;
+            t[0].y += v.y;
         }
         double2 o = acc[e];
-        o.x += re;
-        o.y += im;
+        o.x += (double)((t[0].x + t[1].x) + (t[2].x + t[3].x));
+        o.y += (double)((t[0].y + t[1].y) + (t[2].y + t[3].y));
         acc[e] = o;
     }
 }

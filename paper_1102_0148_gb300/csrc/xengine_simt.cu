@@ -7,7 +7,11 @@
 // V_ij[k] += Y_i conj(Y_j) = (a_i a_j + b_i b_j) + i (b_i a_j - a_i b_j) with
 // Y = a + i b.  One thread owns a 4 x 4 block of antenna pairs (block row
 // bi <= block column bj) of one channel and one range of spectra; the
-// spectra of that channel are staged in shared memory 32 frames at a time.
+// spectra of that channel are staged in shared memory 32 frames at a time,
+// as [frame][plane][antenna] rows of NBP floats (a power of two >= 32) whose
+// 16-byte groups are XOR-swizzled by the frame's group of four: the staging
+// writes (8 lanes per workspace row, 4 frames each) then land on distinct
+// banks, and a thread still reads 4 antennas of a frame as one float4.
 #include "corr_internal.h"
 
 namespace gbcorr {
@@ -15,9 +19,8 @@ namespace {
 
 constexpr int kTS = 32;  // frames per shared-memory tile
 
-__global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt) {
-    extern __shared__ __align__(16) float tile[];  // [kTS][2][NB4]
-    const int NB4 = nb * 4;
+__global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt, int nbp) {
+    extern __shared__ __align__(16) float tile[];  // [kTS][2][nbp], swizzled columns
     const int N = a.N;
     const int k = blockIdx.x;
     const int split = blockIdx.y;
@@ -33,7 +36,8 @@ __global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt) {
         }
         bj = bi + rem;
     }
-    for (int e = threadIdx.x; e < kTS * 2 * NB4; e += blockDim.x) tile[e] = 0.f;
+    // antennas past N (the last block's padding) stay zero
+    for (int e = threadIdx.x; e < kTS * 2 * nbp; e += blockDim.x) tile[e] = 0.f;
 
     float ar[4][4], ai[4][4];
 #pragma unroll
@@ -48,26 +52,33 @@ __global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt) {
     for (int64_t s0 = sb; s0 < se; s0 += kTS) {
         __syncthreads();
         // the tile's 2N rows x 32 frames of channel k are contiguous
-        const float* base = static_cast<const float*>(a.spec) + spec_off(k, 0, s0, N, a.C, 5);
-        for (int e = threadIdx.x; e < 2 * N * kTS; e += blockDim.x) {
-            const int r = e / kTS;
-            const int c = e - r * kTS;
-            const float v = base[e];
+        const float4* base = reinterpret_cast<const float4*>(
+            static_cast<const float*>(a.spec) + spec_off(k, 0, s0, N, a.C, 5));
+        for (int e = threadIdx.x; e < 2 * N * (kTS / 4); e += blockDim.x) {
+            const int r = e >> 3;             // workspace row
+            const int c4 = (e & 7) << 2;      // its frames c4 .. c4 + 3
+            const float4 v = base[e];
             // row r -> (plane, antenna) under the 64-antenna block layout
             const int b = r >> 7;
             const int w = r & 127;
             const int nbk = (N - 64 * b) < 64 ? (N - 64 * b) : 64;
             const int plane = w >= nbk;
-            tile[(c * 2 + plane) * NB4 + 64 * b + w - plane * nbk] = v;
+            float* d = tile + (c4 * 2 + plane) * nbp + ((64 * b + w - plane * nbk) ^ (c4 & 28));
+            d[0] = v.x;
+            d[2 * nbp] = v.y;
+            d[4 * nbp] = v.z;
+            d[6 * nbp] = v.w;
         }
         __syncthreads();
         if (active) {
 #pragma unroll 4
             for (int c = 0; c < kTS; ++c) {
-                const float4 ri = *reinterpret_cast<const float4*>(&tile[(c * 2) * NB4 + 4 * bi]);
-                const float4 ii = *reinterpret_cast<const float4*>(&tile[(c * 2 + 1) * NB4 + 4 * bi]);
-                const float4 rj = *reinterpret_cast<const float4*>(&tile[(c * 2) * NB4 + 4 * bj]);
-                const float4 ij = *reinterpret_cast<const float4*>(&tile[(c * 2 + 1) * NB4 + 4 * bj]);
+                const int sw = c & 28;
+                const int ci = (4 * bi) ^ sw, cj = (4 * bj) ^ sw;
+                const float4 ri = *reinterpret_cast<const float4*>(&tile[(c * 2) * nbp + ci]);
+                const float4 ii = *reinterpret_cast<const float4*>(&tile[(c * 2 + 1) * nbp + ci]);
+                const float4 rj = *reinterpret_cast<const float4*>(&tile[(c * 2) * nbp + cj]);
+                const float4 ij = *reinterpret_cast<const float4*>(&tile[(c * 2 + 1) * nbp + cj]);
                 const float xr[4] = {ri.x, ri.y, ri.z, ri.w};
                 const float xi[4] = {ii.x, ii.y, ii.z, ii.w};
                 const float yr[4] = {rj.x, rj.y, rj.z, rj.w};
@@ -182,11 +193,13 @@ cudaError_t launch_xengine_simt(const XengineArgs& a, cudaStream_t st) {
     const int nt = nb * (nb + 1) / 2;
     int threads = ((nt < 256 ? nt : 256) + 31) / 32 * 32;
     dim3 grid((unsigned)a.C, (unsigned)a.n_split, (unsigned)((nt + threads - 1) / threads));
-    const size_t smem = (size_t)kTS * 2 * nb * 4 * sizeof(float);
+    int nbp = 32;
+    while (nbp < nb * 4) nbp *= 2;
+    const size_t smem = (size_t)kTS * 2 * nbp * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(xengine_simt_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    xengine_simt_kernel<<<grid, threads, smem, st>>>(a, nb, nt);
+    xengine_simt_kernel<<<grid, threads, smem, st>>>(a, nb, nt, nbp);
     return cudaGetLastError();
 }
 

@@ -14,20 +14,29 @@
 // banks, and a thread still reads 4 antennas of a frame as one float4.
 #include "corr_internal.h"
 
+#include <algorithm>
+
 namespace gbcorr {
 namespace {
 
 constexpr int kTS = 32;  // frames per shared-memory tile
 
-__global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt, int nbp) {
-    extern __shared__ __align__(16) float tile[];  // [kTS][2][nbp], swizzled columns
+// A CTA covers G consecutive channels (G > 1 when one channel's nt threads
+// fill less than a CTA; their workspace tiles are adjacent) or, when G = 1,
+// the nt threads of one channel over gridDim.z CTAs.
+__global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt, int nbp, int G) {
+    extern __shared__ __align__(16) float smem_tiles[];  // G x [kTS][2][nbp], swizzled columns
     const int N = a.N;
-    const int k = blockIdx.x;
+    const int g = G > 1 ? threadIdx.x / nt : 0;
+    const int k0 = blockIdx.x * G;
+    const int k = k0 + g;
     const int split = blockIdx.y;
-    const int t = blockIdx.z * blockDim.x + threadIdx.x;
+    const int t = G > 1 ? threadIdx.x - g * nt : blockIdx.z * blockDim.x + threadIdx.x;
+    const int Gc = min(G, a.C - k0);                 // channels this CTA holds
+    float* tile = smem_tiles + (size_t)g * kTS * 2 * nbp;
 
     int bi = 0, bj = 0;
-    const bool active = t < nt;
+    const bool active = t < nt && g < Gc;
     if (active) {
         int rem = t;
         while (rem >= nb - bi) {
@@ -37,7 +46,7 @@ __global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt, int nbp) {
         bj = bi + rem;
     }
     // antennas past N (the last block's padding) stay zero
-    for (int e = threadIdx.x; e < kTS * 2 * nbp; e += blockDim.x) tile[e] = 0.f;
+    for (int e = threadIdx.x; e < G * kTS * 2 * nbp; e += blockDim.x) smem_tiles[e] = 0.f;
 
     float ar[4][4], ai[4][4];
 #pragma unroll
@@ -51,11 +60,14 @@ __global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt, int nbp) {
 
     for (int64_t s0 = sb; s0 < se; s0 += kTS) {
         __syncthreads();
-        // the tile's 2N rows x 32 frames of channel k are contiguous
+        // the tiles' 2N rows x 32 frames of channels k0 .. k0 + Gc - 1 are
+        // contiguous
         const float4* base = reinterpret_cast<const float4*>(
-            static_cast<const float*>(a.spec) + spec_off(k, 0, s0, N, a.C, 5));
-        for (int e = threadIdx.x; e < 2 * N * (kTS / 4); e += blockDim.x) {
-            const int r = e >> 3;             // workspace row
+            static_cast<const float*>(a.spec) + spec_off(k0, 0, s0, N, a.C, 5));
+        for (int e = threadIdx.x; e < Gc * 2 * N * (kTS / 4); e += blockDim.x) {
+            const int rg = e >> 3;            // workspace row of channel k0 + gg
+            const int gg = rg / (2 * N);
+            const int r = rg - gg * 2 * N;
             const int c4 = (e & 7) << 2;      // its frames c4 .. c4 + 3
             const float4 v = base[e];
             // row r -> (plane, antenna) under the 64-antenna block layout
@@ -63,7 +75,8 @@ __global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt, int nbp) {
             const int w = r & 127;
             const int nbk = (N - 64 * b) < 64 ? (N - 64 * b) : 64;
             const int plane = w >= nbk;
-            float* d = tile + (c4 * 2 + plane) * nbp + ((64 * b + w - plane * nbk) ^ (c4 & 28));
+            float* d = smem_tiles + (size_t)gg * kTS * 2 * nbp + (c4 * 2 + plane) * nbp +
+                       ((64 * b + w - plane * nbk) ^ (c4 & 28));
             d[0] = v.x;
             d[2 * nbp] = v.y;
             d[4 * nbp] = v.z;
@@ -191,15 +204,21 @@ cudaError_t launch_xengine_simt(const XengineArgs& a, cudaStream_t st) {
     if (a.spec_type != SPEC_F32) return cudaErrorInvalidValue;
     const int nb = (a.N + 3) / 4;
     const int nt = nb * (nb + 1) / 2;
-    int threads = ((nt < 256 ? nt : 256) + 31) / 32 * 32;
-    dim3 grid((unsigned)a.C, (unsigned)a.n_split, (unsigned)((nt + threads - 1) / threads));
     int nbp = 32;
     while (nbp < nb * 4) nbp *= 2;
-    const size_t smem = (size_t)kTS * 2 * nbp * sizeof(float);
+    const size_t tile_bytes = (size_t)kTS * 2 * nbp * sizeof(float);
+    // channels per CTA: up to 256 threads and 64 KB of tiles
+    int G = nt < 256 ? 256 / nt : 1;
+    G = std::min<int>(G, (int)((64 << 10) / tile_bytes));
+    G = std::max(1, std::min(G, a.C));
+    int threads = G > 1 ? (G * nt + 31) / 32 * 32 : ((nt < 256 ? nt : 256) + 31) / 32 * 32;
+    dim3 grid((unsigned)((a.C + G - 1) / G), (unsigned)a.n_split,
+              (unsigned)(G > 1 ? 1 : (nt + threads - 1) / threads));
+    const size_t smem = G * tile_bytes;
     cudaError_t e = cudaFuncSetAttribute(xengine_simt_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    xengine_simt_kernel<<<grid, threads, smem, st>>>(a, nb, nt, nbp);
+    xengine_simt_kernel<<<grid, threads, smem, st>>>(a, nb, nt, nbp, G);
     return cudaGetLastError();
 }
 

@@ -257,8 +257,8 @@ constexpr int kOutDebug = -1;
 // complex = 544 floats) at the 16-byte aligned offset f mod 4 within row f.
 // A group exchanges through the row of its second frame: during the first
 // round no group writes that row, and in the second the group itself writes
-// it only after its exchange.  No other shared memory is needed, so three
-// CTAs fit on an SM.
+// it only after its exchange.  With the 1 KB table of twiddle bases that is
+// all the shared memory (71 KB), so three CTAs fit on an SM.
 constexpr int kStgRow = 547;
 constexpr int kStgFloats = kF512Frames * kStgRow;
 static_assert(kStgRow % 32 == 3 && kStgRow >= 16 * kXStride * 2 + 3, "staging row layout");

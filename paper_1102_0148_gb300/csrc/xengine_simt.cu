@@ -24,7 +24,9 @@ constexpr int kTS = 32;  // frames per shared-memory tile
 // A CTA covers G consecutive channels (G > 1 when one channel's nt threads
 // fill less than a CTA; their workspace tiles are adjacent) or, when G = 1,
 // the nt threads of one channel over gridDim.z CTAs.
-__global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt, int nbp, int G) {
+template <int NBP>
+__global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt, int G) {
+    constexpr int nbp = NBP;
     extern __shared__ __align__(16) float smem_tiles[];  // G x [kTS][2][nbp], swizzled columns
     const int N = a.N;
     const int g = G > 1 ? threadIdx.x / nt : 0;
@@ -84,27 +86,32 @@ __global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt, int nbp, int 
         }
         __syncthreads();
         if (active) {
-#pragma unroll 4
-            for (int c = 0; c < kTS; ++c) {
-                const int sw = c & 28;
-                const int ci = (4 * bi) ^ sw, cj = (4 * bj) ^ sw;
-                const float4 ri = *reinterpret_cast<const float4*>(&tile[(c * 2) * nbp + ci]);
-                const float4 ii = *reinterpret_cast<const float4*>(&tile[(c * 2 + 1) * nbp + ci]);
-                const float4 rj = *reinterpret_cast<const float4*>(&tile[(c * 2) * nbp + cj]);
-                const float4 ij = *reinterpret_cast<const float4*>(&tile[(c * 2 + 1) * nbp + cj]);
-                const float xr[4] = {ri.x, ri.y, ri.z, ri.w};
-                const float xi[4] = {ii.x, ii.y, ii.z, ii.w};
-                const float yr[4] = {rj.x, rj.y, rj.z, rj.w};
-                const float yi[4] = {ij.x, ij.y, ij.z, ij.w};
+            // frames c4 .. c4 + 3 share one swizzle, so their addresses are
+            // two pointers plus constant offsets
+#pragma unroll 1
+            for (int c4 = 0; c4 < kTS; c4 += 4) {
+                const float* pi = tile + (c4 * 2) * nbp + ((4 * bi) ^ c4);
+                const float* pj = tile + (c4 * 2) * nbp + ((4 * bj) ^ c4);
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int f = 0; f < 4; ++f) {
+                    const float4 ri = *reinterpret_cast<const float4*>(pi + (2 * f) * nbp);
+                    const float4 ii = *reinterpret_cast<const float4*>(pi + (2 * f + 1) * nbp);
+                    const float4 rj = *reinterpret_cast<const float4*>(pj + (2 * f) * nbp);
+                    const float4 ij = *reinterpret_cast<const float4*>(pj + (2 * f + 1) * nbp);
+                    const float xr[4] = {ri.x, ri.y, ri.z, ri.w};
+                    const float xi[4] = {ii.x, ii.y, ii.z, ii.w};
+                    const float yr[4] = {rj.x, rj.y, rj.z, rj.w};
+                    const float yi[4] = {ij.x, ij.y, ij.z, ij.w};
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        ar[u][v] = fmaf(xr[u], yr[v], ar[u][v]);
-                        ar[u][v] = fmaf(xi[u], yi[v], ar[u][v]);
-                        ai[u][v] = fmaf(xi[u], yr[v], ai[u][v]);
-                        ai[u][v] = fmaf(-xr[u], yi[v], ai[u][v]);
-                    }
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            ar[u][v] = fmaf(xr[u], yr[v], ar[u][v]);
+                            ar[u][v] = fmaf(xi[u], yi[v], ar[u][v]);
+                            ai[u][v] = fmaf(xi[u], yr[v], ai[u][v]);
+                            ai[u][v] = fmaf(-xr[u], yi[v], ai[u][v]);
+                        }
+                }
             }
         }
     }
@@ -215,11 +222,20 @@ cudaError_t launch_xengine_simt(const XengineArgs& a, cudaStream_t st) {
     dim3 grid((unsigned)((a.C + G - 1) / G), (unsigned)a.n_split,
               (unsigned)(G > 1 ? 1 : (nt + threads - 1) / threads));
     const size_t smem = G * tile_bytes;
-    cudaError_t e = cudaFuncSetAttribute(xengine_simt_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    xengine_simt_kernel<<<grid, threads, smem, st>>>(a, nb, nt, nbp, G);
-    return cudaGetLastError();
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, threads, smem, st>>>(a, nb, nt, G);
+        return cudaGetLastError();
+    };
+    switch (nbp) {
+        case 32: return go(xengine_simt_kernel<32>);
+        case 64: return go(xengine_simt_kernel<64>);
+        case 128: return go(xengine_simt_kernel<128>);
+        case 256: return go(xengine_simt_kernel<256>);
+        default: return go(xengine_simt_kernel<512>);
+    }
 }
 
 cudaError_t launch_reduce_partials(const float2* partial, int n_split, int64_t CP, double2* acc,

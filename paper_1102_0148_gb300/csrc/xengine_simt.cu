@@ -66,23 +66,24 @@ __global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt, int G) {
         // contiguous
         const float4* base = reinterpret_cast<const float4*>(
             static_cast<const float*>(a.spec) + spec_off(k0, 0, s0, N, a.C, 5));
-        for (int e = threadIdx.x; e < Gc * 2 * N * (kTS / 4); e += blockDim.x) {
-            const int rg = e >> 3;            // workspace row of channel k0 + gg
-            const int gg = rg / (2 * N);
-            const int r = rg - gg * 2 * N;
-            const int c4 = (e & 7) << 2;      // its frames c4 .. c4 + 3
-            const float4 v = base[e];
-            // row r -> (plane, antenna) under the 64-antenna block layout
-            const int b = r >> 7;
-            const int w = r & 127;
-            const int nbk = (N - 64 * b) < 64 ? (N - 64 * b) : 64;
-            const int plane = w >= nbk;
-            float* d = smem_tiles + (size_t)gg * kTS * 2 * nbp + (c4 * 2 + plane) * nbp +
-                       ((64 * b + w - plane * nbk) ^ (c4 & 28));
-            d[0] = v.x;
-            d[2 * nbp] = v.y;
-            d[4 * nbp] = v.z;
-            d[6 * nbp] = v.w;
+        for (int gg = 0; gg < Gc; ++gg) {
+            const float4* bg = base + gg * 2 * N * (kTS / 4);
+            float* tg = smem_tiles + gg * kTS * 2 * nbp;
+            for (int e = threadIdx.x; e < 2 * N * (kTS / 4); e += blockDim.x) {
+                const int r = e >> 3;             // workspace row of channel k0 + gg
+                const int c4 = (e & 7) << 2;      // its frames c4 .. c4 + 3
+                const float4 v = bg[e];
+                // row r -> (plane, antenna) under the 64-antenna block layout
+                const int b = r >> 7;
+                const int w = r & 127;
+                const int nbk = (N - 64 * b) < 64 ? (N - 64 * b) : 64;
+                const int plane = w >= nbk;
+                float* d = tg + (c4 * 2 + plane) * nbp + ((64 * b + w - plane * nbk) ^ c4);
+                d[0] = v.x;
+                d[2 * nbp] = v.y;
+                d[4 * nbp] = v.z;
+                d[6 * nbp] = v.w;
+            }
         }
         __syncthreads();
         if (active) {

@@ -289,11 +289,11 @@ int estimate_scales(corr_t h, const uint8_t* din, int64_t S) {
 // S frames rounded up to whole kSpecPad-frame blocks (the padding frames are zero).
 int64_t pad_frames(int64_t S) { return (S + kSpecPad - 1) / kSpecPad * kSpecPad; }
 
-// F-engine of S frames at `din` (device) into the workspace from frame `off`;
-// raw = true skips the per-antenna corrections (the uncorrected visibilities
-// corr_grad needs).  side = true queues it on the next side stream after the
-// work already on the handle's stream.
-int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off, bool side) {
+// F-engine of S frames at `din` (device) into the workspace from frame `off`,
+// queued on the next side stream after the work already on the handle's
+// stream; raw = true skips the per-antenna corrections (the uncorrected
+// visibilities corr_grad needs).
+int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off) {
     const int64_t S_pad = pad_frames(S);
     if (narrow(h) && !h->scales_ready) {
         int rc = estimate_scales(h, din, S);
@@ -313,13 +313,6 @@ int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off,
     fa.spec_type = h->spec_type;
     fa.scale = (h->spec_type == SPEC_F16 || h->spec_type == SPEC_F8) ? h->scale : nullptr;
     fa.debug_out = nullptr;
-    if (!side) {
-        prof_begin(h);
-        CUDA_TRY(h, launch_fengine(fa, h->stream));
-        prof_end(h, CORR_KERNEL_FENGINE);
-        h->f_last = h->stream;
-        return CORR_OK;
-    }
     const int j = h->f_next;
     cudaStream_t st = h->f_stream[j];
     if (h->prof_on && !h->f_span) {
@@ -409,7 +402,7 @@ int stage_frames(corr_t h, const uint8_t* din, int64_t S, bool raw, double2* acc
         if (rc != CORR_OK) return rc;
     }
     h->fill_acc = acc;
-    int rc = fengine_pass(h, din, S, raw, h->fill, true);
+    int rc = fengine_pass(h, din, S, raw, h->fill);
     if (rc != CORR_OK) return rc;
     const bool whole = S % kSpecPad == 0;
     h->fill += whole ? S : pad_frames(S);
@@ -1152,7 +1145,7 @@ int batch_enqueue(corr_batch_t b, const uint8_t* const* samples, const int64_t* 
             if (f0 >= frames[m]) continue;
             const int64_t S = std::min(h->cap, frames[m] - f0);
             const int64_t rec = (int64_t)h->N * (h->K / 2);
-            int rc = fengine_pass(h, samples[m] + f0 * rec, S, false, 0, true);
+            int rc = fengine_pass(h, samples[m] + f0 * rec, S, false, 0);
             if (rc != CORR_OK) return batch_from_handle(b, m, rc);
             TcRun r{};
             r.S_pad = pad_frames(S);

@@ -367,6 +367,7 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* stg = reinterpret_cast<float*>(smem_raw);                        // [32][547]
     float2* tw_base = reinterpret_cast<float2*>(stg + kStgFloats);          // [2][4 m][16 t]
+    float* sc_tab = reinterpret_cast<float*>(tw_base + 128);                // [256] (FP16/FP8)
 
     const int tid = threadIdx.x;
     const int lane = tid & 15;
@@ -389,6 +390,8 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
         const int j = tid >> 6, m = (tid >> 4) & 3, t = tid & 15;
         tw_base[tid] = a.twiddle[2 * t * m * (j ? 4 : 1)];   // W256^{t m 4^j}
     }
+    // the antenna's pre-cast scales, read once per CTA instead of per output
+    if (OUT == SPEC_F16 || OUT == SPEC_F8) sc_tab[tid] = __ldg(a.scale + (int64_t)i * 256 + tid);
     const float2 wt = __ldg(a.twiddle + lane);
     const float2 u = make_float2(chalf * wt.x, chalf * wt.y);   // c W512^t
 
@@ -455,7 +458,7 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
                 if (s < a.S) a.debug_out[((int64_t)i * a.S + s) * 256 + k] = X;
             } else {
                 if (OUT == SPEC_F16 || OUT == SPEC_F8) {
-                    const float sc = __ldg(a.scale + (int64_t)i * 256 + k);
+                    const float sc = sc_tab[k];
                     X.x *= sc;
                     X.y *= sc;
                 }
@@ -897,9 +900,10 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
         const int64_t fr = dbg ? a.S : a.S_pad;
         if (fr <= 0) return cudaSuccess;
         dim3 grid((unsigned)((fr + kF512Frames - 1) / kF512Frames), (unsigned)a.N);
-        // staging (also the exchange areas) and the twiddle bases, for the
-        // debug output too
-        const size_t smem = (size_t)kStgFloats * sizeof(float) + 128 * sizeof(float2);
+        // staging (also the exchange areas), the twiddle bases and the scales,
+        // for the debug output too
+        const size_t smem = (size_t)kStgFloats * sizeof(float) + 128 * sizeof(float2) +
+                            256 * sizeof(float);
         auto go = [&](auto kern) -> cudaError_t {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);

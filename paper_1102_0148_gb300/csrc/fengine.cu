@@ -257,8 +257,9 @@ constexpr int kOutDebug = -1;
 // complex = 544 floats) at the 16-byte aligned offset f mod 4 within row f.
 // A group exchanges through the row of its second frame: during the first
 // round no group writes that row, and in the second the group itself writes
-// it only after its exchange.  With the 1 KB table of twiddle bases that is
-// all the shared memory (71 KB), so three CTAs fit on an SM.
+// it only after its exchange.  With 4 KB of tables (twiddle bases, scales,
+// corrections) that is all the shared memory (72 KB), so three CTAs fit on
+// an SM.
 constexpr int kStgRow = 547;
 constexpr int kStgFloats = kF512Frames * kStgRow;
 static_assert(kStgRow % 32 == 3 && kStgRow >= 16 * kXStride * 2 + 3, "staging row layout");
@@ -368,6 +369,7 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
     float* stg = reinterpret_cast<float*>(smem_raw);                        // [32][547]
     float2* tw_base = reinterpret_cast<float2*>(stg + kStgFloats);          // [2][4 m][16 t]
     float* sc_tab = reinterpret_cast<float*>(tw_base + 128);                // [256] (FP16/FP8)
+    float2* corr_tab = reinterpret_cast<float2*>(sc_tab + 256);             // [256] corrections
 
     const int tid = threadIdx.x;
     const int lane = tid & 15;
@@ -390,8 +392,10 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
         const int j = tid >> 6, m = (tid >> 4) & 3, t = tid & 15;
         tw_base[tid] = a.twiddle[2 * t * m * (j ? 4 : 1)];   // W256^{t m 4^j}
     }
-    // the antenna's pre-cast scales, read once per CTA instead of per output
+    // the antenna's pre-cast scales and corrections, read once per CTA
+    // instead of per output
     if (OUT == SPEC_F16 || OUT == SPEC_F8) sc_tab[tid] = __ldg(a.scale + (int64_t)i * 256 + tid);
+    if (a.corr) corr_tab[tid] = __ldg(a.corr + (int64_t)i * 256 + tid);
     const float2 wt = __ldg(a.twiddle + lane);
     const float2 u = make_float2(chalf * wt.x, chalf * wt.y);   // c W512^t
 
@@ -453,7 +457,7 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
         // in place of the dropped Nyquist term, X[128] = post conj Z[128].
         const int src = (16 - lane) & 15;
         auto emit = [&](int k, float2 X) {
-            if (a.corr) X = cmul(__ldg(a.corr + (int64_t)i * 256 + k), X);
+            if (a.corr) X = cmul(corr_tab[k], X);
             if (DEBUG) {
                 if (s < a.S) a.debug_out[((int64_t)i * a.S + s) * 256 + k] = X;
             } else {
@@ -900,10 +904,10 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
         const int64_t fr = dbg ? a.S : a.S_pad;
         if (fr <= 0) return cudaSuccess;
         dim3 grid((unsigned)((fr + kF512Frames - 1) / kF512Frames), (unsigned)a.N);
-        // staging (also the exchange areas), the twiddle bases and the scales,
-        // for the debug output too
+        // staging (also the exchange areas), the twiddle bases, the scales and
+        // the corrections, for the debug output too (72 KB: three CTAs per SM)
         const size_t smem = (size_t)kStgFloats * sizeof(float) + 128 * sizeof(float2) +
-                            256 * sizeof(float);
+                            256 * sizeof(float) + 256 * sizeof(float2);
         auto go = [&](auto kern) -> cudaError_t {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);

@@ -368,8 +368,10 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* stg = reinterpret_cast<float*>(smem_raw);                        // [32][547]
     float2* tw_base = reinterpret_cast<float2*>(stg + kStgFloats);          // [2][4 m][16 t]
-    float* sc_tab = reinterpret_cast<float*>(tw_base + 128);                // [256] (FP16/FP8)
-    float2* corr_tab = reinterpret_cast<float2*>(sc_tab + 256);             // [256] corrections
+    // tables that exist only when used: scales (FP16/FP8), corrections
+    constexpr bool kScaled = OUT == SPEC_F16 || OUT == SPEC_F8;
+    float* sc_tab = reinterpret_cast<float*>(tw_base + 128);                // [256] if kScaled
+    float2* corr_tab = reinterpret_cast<float2*>(sc_tab + (kScaled ? 256 : 0));   // [256] if a.corr
 
     const int tid = threadIdx.x;
     const int lane = tid & 15;
@@ -394,7 +396,7 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
     }
     // the antenna's pre-cast scales and corrections, read once per CTA
     // instead of per output
-    if (OUT == SPEC_F16 || OUT == SPEC_F8) sc_tab[tid] = __ldg(a.scale + (int64_t)i * 256 + tid);
+    if (kScaled) sc_tab[tid] = __ldg(a.scale + (int64_t)i * 256 + tid);
     if (a.corr) corr_tab[tid] = __ldg(a.corr + (int64_t)i * 256 + tid);
     const float2 wt = __ldg(a.twiddle + lane);
     const float2 u = make_float2(chalf * wt.x, chalf * wt.y);   // c W512^t
@@ -540,6 +542,8 @@ __global__ void __launch_bounds__(kF1024Threads, 3) fengine_k1024(FengineArgs a)
     float* stg = reinterpret_cast<float*>(smem_raw);                        // [16][1058]
     float2* tw_base = reinterpret_cast<float2*>(stg + kStg1024Floats);      // [2][4 m][32 t]
     float2* tw32 = tw_base + 256;                                           // [2][16]
+    constexpr bool kScaled = OUT == SPEC_F16 || OUT == SPEC_F8;
+    float* sc_tab = reinterpret_cast<float*>(tw32 + 32);                    // [512] if kScaled
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -559,6 +563,9 @@ __global__ void __launch_bounds__(kF1024Threads, 3) fengine_k1024(FengineArgs a)
     }
     // [2][16]: ones, then W32^{t'} = W1024^{32 t'}
     if (tid < 32) tw32[tid] = tid < 16 ? make_float2(1.0f, 0.0f) : a.twiddle[32 * (tid - 16)];
+    // the antenna's pre-cast scales, read once per CTA instead of per output
+    if (kScaled)
+        for (int e = tid; e < 512; e += kF1024Threads) sc_tab[e] = __ldg(a.scale + (int64_t)i * 512 + e);
     const float2 wl = __ldg(a.twiddle + lane);
     const float2 u = make_float2(chalf * wl.x, chalf * wl.y);   // c W1024^l
 
@@ -633,7 +640,7 @@ __global__ void __launch_bounds__(kF1024Threads, 3) fengine_k1024(FengineArgs a)
                 if (s < a.S) a.debug_out[((int64_t)i * a.S + s) * 512 + k] = X;
             } else {
                 if (OUT == SPEC_F16 || OUT == SPEC_F8) {
-                    const float sc = __ldg(a.scale + (int64_t)i * 512 + k);
+                    const float sc = sc_tab[k];
                     X.x *= sc;
                     X.y *= sc;
                 }
@@ -904,10 +911,13 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
         const int64_t fr = dbg ? a.S : a.S_pad;
         if (fr <= 0) return cudaSuccess;
         dim3 grid((unsigned)((fr + kF512Frames - 1) / kF512Frames), (unsigned)a.N);
-        // staging (also the exchange areas), the twiddle bases, the scales and
-        // the corrections, for the debug output too (72 KB: three CTAs per SM)
+        // staging (also the exchange areas), the twiddle bases, and when used
+        // the scales and the corrections, for the debug output too (at most
+        // 72 KB: three CTAs per SM)
+        const bool scaled = !dbg && (a.spec_type == SPEC_F16 || a.spec_type == SPEC_F8);
         const size_t smem = (size_t)kStgFloats * sizeof(float) + 128 * sizeof(float2) +
-                            256 * sizeof(float) + 256 * sizeof(float2);
+                            (scaled ? 256 * sizeof(float) : 0) +
+                            (a.corr ? 256 * sizeof(float2) : 0);
         auto go = [&](auto kern) -> cudaError_t {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);
@@ -929,7 +939,12 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
         dim3 grid((unsigned)((fr + kF1024Frames - 1) / kF1024Frames), (unsigned)a.N);
         // staging (also the exchange areas) and the twiddle tables, for the
         // debug output too
-        const size_t smem = (size_t)kStg1024Floats * sizeof(float) + (256 + 32) * sizeof(float2);
+        // staging (also the exchange areas), the twiddle tables and for
+        // FP16/FP8 the scales, for the debug output too (at most 71 KB: three
+        // CTAs per SM)
+        const bool scaled = !dbg && (a.spec_type == SPEC_F16 || a.spec_type == SPEC_F8);
+        const size_t smem = (size_t)kStg1024Floats * sizeof(float) + (256 + 32) * sizeof(float2) +
+                            (scaled ? 512 * sizeof(float) : 0);
         auto go = [&](auto kern) -> cudaError_t {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);

@@ -73,6 +73,9 @@ struct FengineArgs {
     const float* scale;      // [N][K/2] pre-cast scale (FP16/FP8 only)
     // Debug layout instead: float2 [N][S][K/2] (spec is ignored when set).
     float2* debug_out;
+    // Set by launch_fengine: the K = 512 grid runs antenna fastest
+    // (blockIdx.x = antenna) unless its frame blocks exceed gridDim.y's limit.
+    int ant_x;
 };
 
 cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st);

@@ -344,7 +344,7 @@ __host__ __device__ constexpr int out_bytes() {
 // 2% slower there in FP32 mode.)
 template <int OUT, int CSTEP, int SROW>
 __device__ __forceinline__ void store_rows(const FengineArgs& a, const float* src, int r0,
-                                           int64_t s, int C) {
+                                           int64_t s, int C, int ant) {
     constexpr int eb = out_bytes<OUT>();
     const int tsh = spec_tile_shift(OUT);
     const int64_t step = ((int64_t)CSTEP * 2 * a.N << tsh) * eb;
@@ -352,7 +352,7 @@ __device__ __forceinline__ void store_rows(const FengineArgs& a, const float* sr
 #pragma unroll 1
     for (int plane = 0; plane < 2; ++plane) {
         char* p = static_cast<char*>(a.spec) +
-                  spec_off(r0, spec_row(plane, blockIdx.y, a.N), s, a.N, C, tsh) * eb;
+                  spec_off(r0, spec_row(plane, ant, a.N), s, a.N, C, tsh) * eb;
 #pragma unroll 1
         for (int j = 0; j < C / CSTEP; ++j) {
             store4p<OUT>(p, lo, src[0], src[SROW], src[2 * SROW], src[3 * SROW]);
@@ -378,8 +378,10 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
     const int grp = tid >> 4;
     const int warp = tid >> 5;
     const int half = grp & 1;
-    const int i = blockIdx.y;
-    const int64_t s0 = (int64_t)blockIdx.x * kF512Frames;
+    // antenna fastest (a.ant_x): neighbouring CTAs read adjacent 256-byte
+    // records of the same frames and write adjacent workspace rows
+    const int i = a.ant_x ? blockIdx.x : blockIdx.y;
+    const int64_t s0 = (int64_t)(a.ant_x ? blockIdx.y : blockIdx.x) * kF512Frames;
     // The 1/16 pre-scale of the two-plane FP16 split is folded into the
     // real-split constants: X = c (zk + conj zc) + w'_k (zk - conj zc) with
     // c = 1/2 and w'_k = W512^k / (2i), both times the pre-scale.
@@ -502,7 +504,7 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
     const int l32 = tid & 31;
     const int m = l32 & 7;
     const int r0 = 4 * warp + (l32 >> 3);
-    store_rows<OUT, 32, kStgRow>(a, stg + 4 * m * kStgRow + r0, r0, a.s_base + s0 + 4 * m, 256);
+    store_rows<OUT, 32, kStgRow>(a, stg + 4 * m * kStgRow + r0, r0, a.s_base + s0 + 4 * m, 256, i);
 }
 
 
@@ -550,8 +552,8 @@ __global__ void __launch_bounds__(kF1024Threads, 3) fengine_k1024(FengineArgs a)
     const int warp = tid >> 5;
     const int k1 = lane & 15;
     const int hh = lane >> 4;
-    const int i = blockIdx.y;
-    const int64_t s0 = (int64_t)blockIdx.x * kF1024Frames;
+    const int i = a.ant_x ? blockIdx.x : blockIdx.y;
+    const int64_t s0 = (int64_t)(a.ant_x ? blockIdx.y : blockIdx.x) * kF1024Frames;
     const float post = OUT == SPEC_F16X2 ? kSplitScale : 1.0f;
     const float chalf = 0.5f * post;
     // Twiddles as in the K = 512 kernel: the stage twiddle W512^{t q},
@@ -910,7 +912,10 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
     if (a.K == 512 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0) {
         const int64_t fr = dbg ? a.S : a.S_pad;
         if (fr <= 0) return cudaSuccess;
-        dim3 grid((unsigned)((fr + kF512Frames - 1) / kF512Frames), (unsigned)a.N);
+        const int64_t nfb = (fr + kF512Frames - 1) / kF512Frames;
+        FengineArgs b = a;
+        b.ant_x = nfb <= 65535;
+        const dim3 grid = b.ant_x ? dim3((unsigned)a.N, (unsigned)nfb) : dim3((unsigned)nfb, (unsigned)a.N);
         // staging (also the exchange areas), the twiddle bases, and when used
         // the scales and the corrections, for the debug output too (at most
         // 72 KB: three CTAs per SM)
@@ -922,7 +927,7 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);
             if (e != cudaSuccess) return e;
-            kern<<<grid, kF512Threads, smem, st>>>(a);
+            kern<<<grid, kF512Threads, smem, st>>>(b);
             return cudaGetLastError();
         };
         if (dbg) return go(fengine_k512<kOutDebug>);
@@ -936,7 +941,11 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
     if (a.K == 1024 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0) {
         const int64_t fr = dbg ? a.S : a.S_pad;
         if (fr <= 0) return cudaSuccess;
-        dim3 grid((unsigned)((fr + kF1024Frames - 1) / kF1024Frames), (unsigned)a.N);
+        // frames fastest here (antenna fastest ran ~1% slower at K = 1024)
+        const int64_t nfb = (fr + kF1024Frames - 1) / kF1024Frames;
+        FengineArgs b = a;
+        b.ant_x = 0;
+        const dim3 grid((unsigned)nfb, (unsigned)a.N);
         // staging (also the exchange areas) and the twiddle tables, for the
         // debug output too
         // staging (also the exchange areas), the twiddle tables and for
@@ -949,7 +958,7 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);
             if (e != cudaSuccess) return e;
-            kern<<<grid, kF1024Threads, smem, st>>>(a);
+            kern<<<grid, kF1024Threads, smem, st>>>(b);
             return cudaGetLastError();
         };
         if (dbg) return go(fengine_k1024<kOutDebug>);

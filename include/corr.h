@@ -257,12 +257,13 @@ int corr_debug_spectra(corr_t h, const uint8_t* samples, int64_t n, float* spect
 /* ------------------------------------------------------------------------
  * Batches: several correlators ("modes", e.g. sub-arrays with different N
  * and K) whose X-engine work runs as ONE persistent tensor-core launch per
- * pass (SURVEY's batching form; the paper's correlator serves one mode).
+ * pass (no counterpart in the paper, whose correlator serves one mode).
  * All modes share the X-engine precision (CORR_FP32, CORR_FP16 or
  * CORR_FP8E4M3) and one non-blocking stream owned by the batch; each mode
  * keeps its own workspace and FP64 accumulators.  Per pass index the
- * F-engine of every mode that has that pass is queued, then one launch
- * covers all of their X-engine work.  With each mode's chunk at least its
+ * F-engine of every mode that has that pass is queued (the modes' F-engines
+ * run side by side on their handles' side streams), then one launch covers
+ * all of their X-engine work.  With each mode's chunk at least its
  * push size (corr_batch_set_chunk), a push is exactly one X-engine launch.
  *
  * corr_batch_create  n_modes in [1, 4]; N[m], K[m] as corr_create.

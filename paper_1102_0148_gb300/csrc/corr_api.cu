@@ -57,6 +57,7 @@ struct corr_s {
     double2* acc = nullptr;      // [C][P]
     double2* acc_raw = nullptr;  // [C][P] uncorrected visibilities for corr_grad
     float2* grad_buf = nullptr;  // device staging for corr_grad's inputs and outputs
+    void* grad_scratch = nullptr; // corr_grad's factor table and partial sums
     float2* partial = nullptr;   // [max_split][C][P]
     int max_split = 0;
     int* status = nullptr;       // device-side error word
@@ -512,6 +513,7 @@ void destroy_impl(corr_t h) {
     cudaFree(h->acc);
     cudaFree(h->acc_raw);
     cudaFree(h->grad_buf);
+    cudaFree(h->grad_scratch);
     cudaFree(h->status);
     cudaFree(h->vis_dev);
     cudaFree(h->sdelay);
@@ -878,6 +880,8 @@ int corr_grad(corr_t h, const uint8_t* samples, int64_t n, const float* gains,
     if (!h->grad_buf)
         CUDA_TRY(h, cudaMalloc((void**)&h->grad_buf, 4 * (size_t)h->N * sizeof(float2) +
                                                      CPb * sizeof(double2)));
+    if (!h->grad_scratch)
+        CUDA_TRY(h, cudaMalloc(&h->grad_scratch, grad_scratch_bytes(h->N, h->K)));
     float2* g_dev = h->grad_buf;
     float* t_dev = reinterpret_cast<float*>(g_dev + h->N);
     float2* gg_dev = g_dev + 2 * h->N;
@@ -901,7 +905,8 @@ int corr_grad(corr_t h, const uint8_t* samples, int64_t n, const float* gains,
         if (rc != CORR_OK) return rc;
     }
     CUDA_TRY(h, launch_grad(h->acc_raw, gv, grad_fp64, gains ? g_dev : nullptr,
-                            delays ? t_dev : nullptr, h->N, h->K, gg_dev, gt_dev, h->stream));
+                            delays ? t_dev : nullptr, h->N, h->K, gg_dev, gt_dev,
+                            h->grad_scratch, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(grad_gains, gg_dev, h->N * sizeof(float2), cudaMemcpyDefault,
                                 h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(grad_delays, gt_dev, h->N * sizeof(float), cudaMemcpyDefault,

@@ -126,7 +126,8 @@ cudaError_t launch_scales_from_autos(const double2* acc, int N, int C, int P, in
 // ([P][C], complex64 or complex128).
 cudaError_t launch_grad(const double2* R, const void* G, int G_fp64, const float2* gains,
                         const float* delays, int N, int K, float2* grad_g, float* grad_tau,
-                        cudaStream_t st);
+                        void* scratch, cudaStream_t st);
+size_t grad_scratch_bytes(int N, int K);   // device scratch launch_grad needs
 
 // Message returned by corr_last_error(NULL) on this thread.
 void set_global_error(const char* msg);

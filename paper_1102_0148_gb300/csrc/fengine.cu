@@ -362,7 +362,10 @@ __device__ __forceinline__ void store_rows(const FengineArgs& a, const float* sr
     }
 }
 
-template <int OUT>
+// CORR: the per-antenna corrections are applied (a.corr set).  A run-time
+// test in the split made the whole kernel 7% slower, so it is a template
+// parameter.
+template <int OUT, bool CORR>
 __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
     constexpr bool DEBUG = OUT == kOutDebug;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -399,7 +402,7 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
     // the antenna's pre-cast scales and corrections, read once per CTA
     // instead of per output
     if (kScaled) sc_tab[tid] = __ldg(a.scale + (int64_t)i * 256 + tid);
-    if (a.corr) corr_tab[tid] = __ldg(a.corr + (int64_t)i * 256 + tid);
+    if (CORR) corr_tab[tid] = __ldg(a.corr + (int64_t)i * 256 + tid);
     const float2 wt = __ldg(a.twiddle + lane);
     const float2 u = make_float2(chalf * wt.x, chalf * wt.y);   // c W512^t
 
@@ -461,7 +464,7 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
         // in place of the dropped Nyquist term, X[128] = post conj Z[128].
         const int src = (16 - lane) & 15;
         auto emit = [&](int k, float2 X) {
-            if (a.corr) X = cmul(corr_tab[k], X);
+            if (CORR) X = cmul(corr_tab[k], X);
             if (DEBUG) {
                 if (s < a.S) a.debug_out[((int64_t)i * a.S + s) * 256 + k] = X;
             } else {
@@ -537,7 +540,7 @@ constexpr int kStg1024Row = 1058;
 constexpr int kStg1024Floats = kF1024Frames * kStg1024Row;
 static_assert(kStg1024Row % 8 == 2 && kStg1024Row >= 16 * kX1024Stride * 2 + 2, "staging row layout");
 
-template <int OUT>
+template <int OUT, bool CORR>
 __global__ void __launch_bounds__(kF1024Threads, 3) fengine_k1024(FengineArgs a) {
     constexpr bool DEBUG = OUT == kOutDebug;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -637,7 +640,7 @@ __global__ void __launch_bounds__(kF1024Threads, 3) fengine_k1024(FengineArgs a)
         // slot 0 makes X[0] and X[256]).
         const int src = (32 - lane) & 31;
         auto emit = [&](int k, float2 X) {
-            if (a.corr) X = cmul(__ldg(a.corr + (int64_t)i * 512 + k), X);
+            if (CORR) X = cmul(__ldg(a.corr + (int64_t)i * 512 + k), X);
             if (DEBUG) {
                 if (s < a.S) a.debug_out[((int64_t)i * a.S + s) * 512 + k] = X;
             } else {
@@ -930,12 +933,13 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
             kern<<<grid, kF512Threads, smem, st>>>(b);
             return cudaGetLastError();
         };
-        if (dbg) return go(fengine_k512<kOutDebug>);
+        auto go2 = [&](auto plain, auto corrected) { return a.corr ? go(corrected) : go(plain); };
+        if (dbg) return go2(fengine_k512<kOutDebug, false>, fengine_k512<kOutDebug, true>);
         switch (a.spec_type) {
-            case SPEC_F32: return go(fengine_k512<SPEC_F32>);
-            case SPEC_F16: return go(fengine_k512<SPEC_F16>);
-            case SPEC_F8: return go(fengine_k512<SPEC_F8>);
-            default: return go(fengine_k512<SPEC_F16X2>);
+            case SPEC_F32: return go2(fengine_k512<SPEC_F32, false>, fengine_k512<SPEC_F32, true>);
+            case SPEC_F16: return go2(fengine_k512<SPEC_F16, false>, fengine_k512<SPEC_F16, true>);
+            case SPEC_F8: return go2(fengine_k512<SPEC_F8, false>, fengine_k512<SPEC_F8, true>);
+            default: return go2(fengine_k512<SPEC_F16X2, false>, fengine_k512<SPEC_F16X2, true>);
         }
     }
     if (a.K == 1024 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0) {
@@ -961,12 +965,13 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
             kern<<<grid, kF1024Threads, smem, st>>>(b);
             return cudaGetLastError();
         };
-        if (dbg) return go(fengine_k1024<kOutDebug>);
+        auto go2 = [&](auto plain, auto corrected) { return a.corr ? go(corrected) : go(plain); };
+        if (dbg) return go2(fengine_k1024<kOutDebug, false>, fengine_k1024<kOutDebug, true>);
         switch (a.spec_type) {
-            case SPEC_F32: return go(fengine_k1024<SPEC_F32>);
-            case SPEC_F16: return go(fengine_k1024<SPEC_F16>);
-            case SPEC_F8: return go(fengine_k1024<SPEC_F8>);
-            default: return go(fengine_k1024<SPEC_F16X2>);
+            case SPEC_F32: return go2(fengine_k1024<SPEC_F32, false>, fengine_k1024<SPEC_F32, true>);
+            case SPEC_F16: return go2(fengine_k1024<SPEC_F16, false>, fengine_k1024<SPEC_F16, true>);
+            case SPEC_F8: return go2(fengine_k1024<SPEC_F8, false>, fengine_k1024<SPEC_F8, true>);
+            default: return go2(fengine_k1024<SPEC_F16X2, false>, fengine_k1024<SPEC_F16X2, true>);
         }
     }
     if ((a.K == 2048 || a.K == 4096) && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0) {

@@ -67,8 +67,10 @@ typedef struct corr_s* corr_t;
 
 /* X-engine input precision. */
 enum corr_dtype {
-    /* FP32-accurate: the F-engine writes FP32 spectra; the X-engine runs on
-       the tensor cores with each operand split into two TF32 terms. */
+    /* FP32-accurate: the F-engine splits each spectrum value, pre-scaled by a
+       power of two per antenna, into two FP16 terms hi + lo (~22 significant
+       bits); the X-engine runs on the tensor cores (kind::f16, hi hi^T +
+       hi lo^T + lo hi^T, FP32 accumulation) and divides the scale out. */
     CORR_FP32 = 0,
     /* Spectra scaled per (antenna, channel) and cast to FP16 / FP8-E4M3 before
        the tensor-core X-engine; FP32 accumulation; descaled at the flush.
@@ -124,7 +126,13 @@ int corr_set_tiles(corr_t h, int window, int stages, int split, int atoms);
 /* Per-antenna corrections of Sec. 2.1.  gains: N complex values as 2N floats
  * (re, im); delays: N floats, in samples.  Either may be NULL (gain 1,
  * delay 0); both NULL switches corrections off.  Host or device memory; the
- * values are copied before return.  Takes effect for spectra pushed later. */
+ * values are copied before return.  Takes effect for spectra pushed later.
+ * Every gain must be finite with |g| = 0 or 2^-40 <= |g| <= 2^40, every
+ * delay finite; otherwise CORR_EINVAL and nothing changes.  (In CORR_FP32
+ * mode each antenna's spectra enter the FP16 planes pre-scaled by the power
+ * of two sigma_i = 2^floor(log2(2^15 / (8 K |g_i|))), which bounds every
+ * scaled value by 2^15 for any 4-bit input and is divided out exactly; when
+ * the gains change sigma, frames already pushed are cross-multiplied first.) */
 int corr_set_corrections(corr_t h, const float* gains, const float* delays);
 
 /* Pre-cast scales of a CORR_FP16 / CORR_FP8E4M3 handle (Sec. 4: the
@@ -321,7 +329,10 @@ const char* corr_batch_last_error(corr_batch_t b);
  * 256 -- are rejected with CORR_EINVAL and a message stating both sizes
  * (N = 44, K = 512 fits).  The first call on each device looks up the
  * array's device address with cudaGetSymbolAddress while that device is
- * current; make that first call before any stream capture.  All calls share
+ * current; make that first call before any stream capture.  The address is
+ * kept with the CUDA context it belongs to; after a device reset the first
+ * call in the new context looks it up again (so, again, before any capture
+ * in that context).  All calls share
  * the one array: calls whose work overlaps on the GPU (different streams, or
  * different host threads) race and must be serialised by the caller.
  * Errors: CORR_EINVAL (arguments or size), CORR_ECUDA; message from

@@ -51,6 +51,11 @@ struct corr_s {
     float2* gains_dev = nullptr;
     float* delays_dev = nullptr;
     float* scale = nullptr;      // [N][C] pre-cast scales (FP16 / FP8)
+    // [2][N] pre-scales sigma_i of the two-plane FP16 split (CORR_FP32): row 0
+    // for unit gains (uncorrected passes), row 1 for the current corrections
+    float* split = nullptr;
+    std::vector<float> split_host;   // row 1 as last uploaded
+    const float* fill_split = nullptr;   // sigma table of the frames waiting in the workspace
     float scale_target = 1.0f;   // rms of each real part after scaling
     bool scales_ready = false;   // scale[] holds valid values
     bool scales_user = false;    // set by corr_set_scales (not updated at dumps)
@@ -290,6 +295,13 @@ int estimate_scales(corr_t h, const uint8_t* din, int64_t S) {
 // S frames rounded up to whole kSpecPad-frame blocks (the padding frames are zero).
 int64_t pad_frames(int64_t S) { return (S + kSpecPad - 1) / kSpecPad * kSpecPad; }
 
+// Two-plane pre-scales of a pass (CORR_FP32 handles; nullptr otherwise):
+// unit gains for uncorrected passes, the current corrections' otherwise.
+const float* split_table(corr_t h, bool raw) {
+    if (!h->split) return nullptr;
+    return raw || !h->corr_on ? h->split : h->split + h->N;
+}
+
 // F-engine of S frames at `din` (device) into the workspace from frame `off`,
 // queued on the next side stream after the work already on the handle's
 // stream; raw = true skips the per-antenna corrections (the uncorrected
@@ -313,6 +325,7 @@ int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off)
     fa.plane_stride = (int64_t)h->C * 2 * h->N * h->cap;
     fa.spec_type = h->spec_type;
     fa.scale = (h->spec_type == SPEC_F16 || h->spec_type == SPEC_F8) ? h->scale : nullptr;
+    fa.split = split_table(h, raw);
     fa.debug_out = nullptr;
     const int j = h->f_next;
     cudaStream_t st = h->f_stream[j];
@@ -350,6 +363,7 @@ int xengine_pass(corr_t h, int64_t S_pad, double2* acc) {
         run.partial = h->partial;
         run.acc = acc;
         run.scale = h->scale;
+        run.split = h->fill_split;
         run.status = h->status;
         TcPlan* plans[1] = {h->tc};
         int rc = tc_launch(plans, 1, &run, h->stream, h->err);
@@ -393,7 +407,8 @@ int flush(corr_t h) {
 // there; the X-engine runs once the workspace is full, or at once when S is
 // not a multiple of the 128-frame padding (the padding must stay at the end).
 int stage_frames(corr_t h, const uint8_t* din, int64_t S, bool raw, double2* acc) {
-    if (h->fill > 0 && acc != h->fill_acc) {
+    const float* split = split_table(h, raw);
+    if (h->fill > 0 && (acc != h->fill_acc || split != h->fill_split)) {
         int rc = flush(h);
         if (rc != CORR_OK) return rc;
     }
@@ -403,6 +418,7 @@ int stage_frames(corr_t h, const uint8_t* din, int64_t S, bool raw, double2* acc
         if (rc != CORR_OK) return rc;
     }
     h->fill_acc = acc;
+    h->fill_split = split;
     int rc = fengine_pass(h, din, S, raw, h->fill);
     if (rc != CORR_OK) return rc;
     const bool whole = S % kSpecPad == 0;
@@ -456,7 +472,7 @@ int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, doubl
         if (rc != CORR_OK) return rc;
     }
     for (int64_t f0 = 0; f0 < frames;) {
-        if (h->fill > 0 && acc != h->fill_acc) {
+        if (h->fill > 0 && (acc != h->fill_acc || split_table(h, raw) != h->fill_split)) {
             int rc = flush(h);
             if (rc != CORR_OK) return rc;
         }
@@ -510,6 +526,7 @@ void destroy_impl(corr_t h) {
     cudaFree(h->gains_dev);
     cudaFree(h->delays_dev);
     cudaFree(h->scale);
+    cudaFree(h->split);
     cudaFree(h->acc);
     cudaFree(h->acc_raw);
     cudaFree(h->grad_buf);
@@ -622,6 +639,17 @@ int corr_create(corr_t* out, int N, int K, int dtype) {
             cudaGetLastError();
             return bail(set_err(h, CORR_ENOMEM, "device allocation failed"));
         }
+    }
+    if (h->spec_type == SPEC_F16X2) {
+        h->split_host.assign(2 * (size_t)N, split_scale_for(1.0, K));
+        if (cudaMalloc((void**)&h->split, 2 * (size_t)N * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(set_err(h, CORR_ENOMEM, "device allocation failed"));
+        }
+        if (cudaMemcpy(h->split, h->split_host.data(), 2 * (size_t)N * sizeof(float),
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(set_err(h, CORR_ECUDA, "initialisation copy failed"));
+        h->split_host.resize(N);
     }
     if (cudaMemcpy(h->twiddle, tw.data(), K * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemsetAsync(h->acc, 0, acc_bytes, h->stream) != cudaSuccess ||
@@ -829,9 +857,49 @@ int corr_set_sample_delays(corr_t h, const int32_t* delays) {
 
 int corr_set_corrections(corr_t h, const float* gains, const float* delays) {
     if (!h) return CORR_EINVAL;
-    // launches already queued keep the old table
+    // Host copies, to check the values and to derive the two-plane pre-scales.
+    std::vector<float> gh, th;
+    if (gains) {
+        gh.resize(2 * (size_t)h->N);
+        CUDA_TRY(h, cudaMemcpy(gh.data(), gains, gh.size() * sizeof(float), cudaMemcpyDefault));
+        for (int i = 0; i < h->N; ++i) {
+            const double a = std::hypot((double)gh[2 * i], (double)gh[2 * i + 1]);
+            if (!std::isfinite(a) || a > kGainMax || (a > 0.0 && a < kGainMin))
+                return set_err(h, CORR_EINVAL,
+                               "gain %d has modulus %g: gains must be finite, 0 or within "
+                               "[2^-40, 2^40]", i, a);
+        }
+    }
+    if (delays) {
+        th.resize(h->N);
+        CUDA_TRY(h, cudaMemcpy(th.data(), delays, th.size() * sizeof(float), cudaMemcpyDefault));
+        for (int i = 0; i < h->N; ++i)
+            if (!std::isfinite(th[i]))
+                return set_err(h, CORR_EINVAL, "delay %d is not finite", i);
+    }
+    // launches already queued keep the old tables
     int jrc = join_fengines(h);
     if (jrc != CORR_OK) return jrc;
+    // Frames already pushed keep the old corrections and pre-scales: with new
+    // pre-scales they are cross-multiplied first.
+    if (h->split) {
+        std::vector<float> sn(h->N, split_scale_for(1.0, h->K));
+        if (gains)
+            for (int i = 0; i < h->N; ++i)
+                sn[i] = split_scale_for(std::hypot((double)gh[2 * i], (double)gh[2 * i + 1]), h->K);
+        const bool on = gains || delays;
+        const bool changed = sn != h->split_host || on != h->corr_on;
+        if (changed && h->fill > 0 && h->fill_split != h->split) {
+            int frc = flush(h);
+            if (frc != CORR_OK) return frc;
+        }
+        if (sn != h->split_host) {
+            CUDA_TRY(h, cudaMemcpyAsync(h->split + h->N, sn.data(), h->N * sizeof(float),
+                                        cudaMemcpyHostToDevice, h->stream));
+            CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+            h->split_host = sn;
+        }
+    }
     if (!gains && !delays) {
         h->corr_on = false;
         return CORR_OK;
@@ -1157,6 +1225,7 @@ int batch_enqueue(corr_batch_t b, const uint8_t* const* samples, const int64_t* 
             r.partial = h->partial;
             r.acc = h->acc;
             r.scale = h->scale;
+            r.split = split_table(h, false);
             r.status = h->status;
             plans[na] = h->tc;
             runs[na] = r;

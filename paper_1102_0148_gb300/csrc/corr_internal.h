@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
+#include <cmath>
 #include <cstdint>
 #include <string>
 
@@ -14,7 +15,8 @@ namespace gbcorr {
 //   SPEC_F32    one FP32 plane (CUDA-core X-engine)
 //   SPEC_F16    one FP16 plane of scaled values (precision form)
 //   SPEC_F8     one FP8-E4M3 plane of scaled values (precision form)
-//   SPEC_F16X2  two FP16 planes, hi = fp16(x/16) and lo = fp16(x/16 - hi):
+//   SPEC_F16X2  two FP16 planes, hi = fp16(sigma_i x) and lo = fp16(sigma_i x - hi)
+//               with the antenna's power-of-two pre-scale sigma_i (below):
 //               ~22 significant bits, the FP32-accurate tensor-core input
 enum SpecType { SPEC_F32 = 0, SPEC_F16 = 1, SPEC_F8 = 2, SPEC_F16X2 = 3 };
 
@@ -33,9 +35,27 @@ __host__ __device__ __forceinline__ int spec_row(int plane, int i, int N) {
     return 128 * b + plane * nb + (i & 63);
 }
 
-// Pre-scale of the two-plane FP16 split; keeps |x|/16 below the FP16 range
-// limit for every 4-bit input up to K = 4096 (|X| <= 8K) with |g| < 3.
-constexpr float kSplitScale = 0.0625f;
+// Pre-scale of the two-plane FP16 split (SPEC_F16X2), one power of two per
+// antenna.  A 4-bit input bounds every transform value, |X[k]| <= 8K (all
+// samples -8), and a correction keeps |Y| = |a_i[k]| |X| = |g_i| |X|, so
+//   sigma_i = 2^floor(log2(2^15 / (8 K |g_i|)))
+// puts every sigma_i |Y| at or below 2^15, half the FP16 range limit (65504),
+// whatever the gain, while the typical value (rms ~ sqrt(K) 2 |g_i|) stays
+// hundreds of times above the FP16 subnormal range.  Powers of two make the
+// scaling and the descaling by 1/(sigma_i sigma_j) in the X-engine exact.
+// The exponent is clamped to [-60, 60] (zero gain takes 2^60).
+constexpr double kSplitBound = 32768.0;
+constexpr int kSplitExpMax = 60;
+inline float split_scale_for(double gabs, int K) {
+    if (!(gabs > 0.0)) return ldexpf(1.0f, kSplitExpMax);
+    int e = (int)floor(log2(kSplitBound / (8.0 * K * gabs)));
+    e = e < -kSplitExpMax ? -kSplitExpMax : (e > kSplitExpMax ? kSplitExpMax : e);
+    return ldexpf(1.0f, e);
+}
+// Gains accepted by corr_set_corrections: 0 or 2^-40 <= |g| <= 2^40 (finite),
+// so the descaled visibilities stay inside the FP32 range.
+constexpr double kGainMin = 9.094947017729282e-13;   // 2^-40
+constexpr double kGainMax = 1099511627776.0;         // 2^40
 
 // Spectra are padded with zero frames up to a multiple of this many frames,
 // so every X-engine tile along the spectrum axis is whole.
@@ -71,6 +91,7 @@ struct FengineArgs {
     int64_t plane_stride;    // elements from the hi plane to the lo plane (SPEC_F16X2)
     int spec_type;
     const float* scale;      // [N][K/2] pre-cast scale (FP16/FP8 only)
+    const float* split;      // [N] pre-scale sigma_i of the two-plane split (SPEC_F16X2 only)
     // Debug layout instead: float2 [N][S][K/2] (spec is ignored when set).
     float2* debug_out;
     // Set by launch_fengine: the K = 512 grid runs antenna fastest

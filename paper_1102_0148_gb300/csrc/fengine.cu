@@ -29,11 +29,11 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float nib(unsigned v) { return (float)((int)((v ^ 8u) & 15u) - 8); }
 
 __device__ __forceinline__ void store_spec(void* spec, int t, int64_t off, float v,
-                                           int64_t plane_stride) {
+                                           int64_t plane_stride, float sigma) {
     if (t == SPEC_F32) {
         static_cast<float*>(spec)[off] = v;
     } else if (t == SPEC_F16X2) {
-        const float xs = v * kSplitScale;
+        const float xs = v * sigma;
         const __half hi = __float2half_rn(xs);
         const __half lo = __float2half_rn(xs - __half2float(hi));
         static_cast<__half*>(spec)[off] = hi;
@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(kThreads) fengine_generic(FengineArgs a, int F
         __syncthreads();
     }
     if (!DEBUG) {
+        const float sigma = a.spec_type == SPEC_F16X2 ? __ldg(a.split + i) : 1.0f;
         const int nfr = (int)min((int64_t)FT, a.S_pad - s0);
         for (int e = tid; e < 2 * C * FT; e += kThreads) {
             const int row = e / FT;
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) fengine_generic(FengineArgs a, int F
             const int k = row - plane * C;
             const int64_t off = spec_off(k, spec_row(plane, i, a.N), a.s_base + s0 + f, a.N, C,
                                          spec_tile_shift(a.spec_type));
-            store_spec(a.spec, a.spec_type, off, stg[row * FT + f], a.plane_stride);
+            store_spec(a.spec, a.spec_type, off, stg[row * FT + f], a.plane_stride, sigma);
         }
     }
 }
@@ -282,7 +283,7 @@ __device__ __forceinline__ void store4(void* spec, int64_t off, int64_t plane_st
         const __nv_fp8x2_storage_t b = __nv_cvt_float2_to_fp8x2(make_float2(v2, v3), __NV_SATFINITE, __NV_E4M3);
         *reinterpret_cast<unsigned*>(static_cast<unsigned char*>(spec) + off) =
             (unsigned)a | ((unsigned)b << 16);
-    } else {  // SPEC_F16X2: values already carry the 1/16 pre-scale
+    } else {  // SPEC_F16X2: values already carry the pre-scale sigma_i
         const __half2 ha = __floats2half2_rn(v0, v1), hb = __floats2half2_rn(v2, v3);
         const float2 fa = __half22float2(ha), fb = __half22float2(hb);
         const __half2 la = __floats2half2_rn(v0 - fa.x, v1 - fa.y);
@@ -314,7 +315,7 @@ __device__ __forceinline__ void store4p(char* p, int64_t lo, float v0, float v1,
         const __nv_fp8x2_storage_t a = __nv_cvt_float2_to_fp8x2(make_float2(v0, v1), __NV_SATFINITE, __NV_E4M3);
         const __nv_fp8x2_storage_t b = __nv_cvt_float2_to_fp8x2(make_float2(v2, v3), __NV_SATFINITE, __NV_E4M3);
         *reinterpret_cast<unsigned*>(p) = (unsigned)a | ((unsigned)b << 16);
-    } else {  // SPEC_F16X2: values already carry the 1/16 pre-scale
+    } else {  // SPEC_F16X2: values already carry the pre-scale sigma_i
         const __half2 ha = __floats2half2_rn(v0, v1), hb = __floats2half2_rn(v2, v3);
         const float2 fa = __half22float2(ha), fb = __half22float2(hb);
         const __half2 la = __floats2half2_rn(v0 - fa.x, v1 - fa.y);
@@ -385,10 +386,10 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
     // records of the same frames and write adjacent workspace rows
     const int i = a.ant_x ? blockIdx.x : blockIdx.y;
     const int64_t s0 = (int64_t)(a.ant_x ? blockIdx.y : blockIdx.x) * kF512Frames;
-    // The 1/16 pre-scale of the two-plane FP16 split is folded into the
-    // real-split constants: X = c (zk + conj zc) + w'_k (zk - conj zc) with
-    // c = 1/2 and w'_k = W512^k / (2i), both times the pre-scale.
-    const float post = OUT == SPEC_F16X2 ? kSplitScale : 1.0f;
+    // The antenna's pre-scale sigma_i of the two-plane FP16 split is folded
+    // into the real-split constants: X = c (zk + conj zc) + w'_k (zk - conj zc)
+    // with c = 1/2 and w'_k = W512^k / (2i), both times the pre-scale.
+    const float post = OUT == SPEC_F16X2 ? __ldg(a.split + i) : 1.0f;
     const float chalf = 0.5f * post;
 
     // Twiddles, kept off the shared-memory pipe where arithmetic can stand
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(kF1024Threads, 3) fengine_k1024(FengineArgs a)
     const int hh = lane >> 4;
     const int i = a.ant_x ? blockIdx.x : blockIdx.y;
     const int64_t s0 = (int64_t)(a.ant_x ? blockIdx.y : blockIdx.x) * kF1024Frames;
-    const float post = OUT == SPEC_F16X2 ? kSplitScale : 1.0f;
+    const float post = OUT == SPEC_F16X2 ? __ldg(a.split + i) : 1.0f;
     const float chalf = 0.5f * post;
     // Twiddles as in the K = 512 kernel: the stage twiddle W512^{t q},
     // q = p + 4 r, is W512^{t p} W512^{4 t r} from a table of the six bases,
@@ -779,7 +780,7 @@ __global__ void __launch_bounds__(kRadThreads, 1) fengine_rad16(FengineArgs a) {
     const int t = tid - g * B;
     const int i = blockIdx.y;
     const int64_t s0 = (int64_t)blockIdx.x * FT;
-    const float post = OUT == SPEC_F16X2 ? kSplitScale : 1.0f;
+    const float post = OUT == SPEC_F16X2 ? __ldg(a.split + i) : 1.0f;
     const float chalf = 0.5f * post;
 
     // W_L^{t k1} = W_K^{2 t k1 mod K};  W_B^{r k2} = W_K^{32 r k2}

@@ -17,10 +17,11 @@
 // both operands are the same shared-memory tile.
 //
 // Precisions (operands in shared memory, K-major, 128-byte swizzle):
-//   mode 0 (FP32-accurate): two FP16 planes x/16 = hi + lo.  Diagonal pairs
-//           issue Dhh += hi hi^T and Dhl += hi lo^T and form
-//           G = 256 (Dhh + Dhl + Dhl^T); off-diagonal pairs issue hi hi^T,
-//           hi lo^T and lo hi^T into one accumulator (lo lo^T is below 2^-22).
+//   mode 0 (FP32-accurate): two FP16 planes sigma_i x = hi + lo, sigma_i a
+//           power of two per antenna.  Diagonal pairs issue Dhh += hi hi^T
+//           and Dhl += hi lo^T and form G = Dhh + Dhl + Dhl^T; off-diagonal
+//           pairs issue hi hi^T, hi lo^T and lo hi^T into one accumulator
+//           (lo lo^T is below 2^-22); V_ij is descaled by 1/(sigma_i sigma_j).
 //   mode 1: one FP16 plane (pre-scaled per antenna and channel).
 //   mode 2: one FP8-E4M3 plane (pre-scaled), kind::f8f6f4.
 //
@@ -73,6 +74,7 @@ struct TcModeArgs {
     double2* acc;             // [C][P] FP64 accumulator
     int* ticket;              // [C][npairs] arrival counters (n_split > 1), zero between launches
     const float* scale;       // [N][C] pre-cast scales (modes 1, 2)
+    const float* split;       // [N] two-plane pre-scales sigma_i (mode 0)
 };
 
 struct TcArgs {
@@ -683,7 +685,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                 }
                 epi_sync();
             }
-            const float gs = MODE == 0 ? 1.0f / (kSplitScale * kSplitScale) : 1.0f;
             const int N = d.N, C = d.C, P = d.P;
             const int npl = diag ? nb1 * (nb1 + 1) / 2 : nb1 * nb2;
             const bool direct = pc.nslots == 1;
@@ -716,8 +717,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                             const float im = Gs[(nb1 + li) * ldg + lj] - Gs[li * ldg + nb2 + lj];
                             const int i = 64 * itm.b1 + li;
                             const int j = 64 * itm.b2 + lj;
-                            float f = gs;
-                            if (MODE != 0)
+                            float f;
+                            if (MODE == 0)
+                                f = 1.0f / (__ldg(d.split + i) * __ldg(d.split + j));
+                            else
                                 f = 1.0f / (__ldg(d.scale + (int64_t)i * C + itm.k) *
                                             __ldg(d.scale + (int64_t)j * C + itm.k));
                             pp[u] = i * N - i * (i - 1) / 2 + (j - i);
@@ -1197,6 +1200,7 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
         d.acc = runs[m].acc;
         d.ticket = plans[m]->ticket;
         d.scale = runs[m].scale;
+        d.split = runs[m].split;
         d.tiles = d.S_pad / p->KT;
         d.cap_tiles = (int)(p->cap / p->KT);
         d.box_bytes = (uint32_t)p->box_rows * kRowBytes;

@@ -17,6 +17,7 @@ struct TcRun {
     float2* partial;          // [max_split][C][P] partials, used when n_split > 1
     double2* acc;             // [C][P] FP64 accumulator, added to when n_split == 1
     const float* scale;       // [N][C] pre-cast scales (FP16 / FP8), else nullptr
+    const float* split;       // [N] two-plane pre-scales sigma_i (FP32 mode), else nullptr
     int* status;              // device status word (bounded waits)
     int n_split;              // out: ranges per channel (combined in the kernel)
     bool direct;              // out: accumulated into acc (no reduction needed)

@@ -10,6 +10,8 @@
 // carved out of one fixed array compiled into this library.
 #include "corr_internal.h"
 
+#include <cuda.h>
+
 #include <cstdio>
 #include <mutex>
 
@@ -24,10 +26,34 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Device address of g_noalloc_scratch per device.  In host code the array's
 // name is only a host-side stand-in; its device address comes from
-// cudaGetSymbolAddress, looked up once per device.
+// cudaGetSymbolAddress, looked up once per device and context: the context
+// it was looked up in is kept beside it, and a different current context
+// (the device was reset and its context re-created, which can load the
+// module at another address) triggers a fresh lookup.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+// The driver's cuCtxGetCurrent, reached through the runtime's entry-point
+// query (the library links no driver import library).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
 
 constexpr int64_t kSplit = 256;     // frames per X-engine split, as the SIMT handle path
 constexpr int64_t kMaxPass = 2048;  // frames per pass at most
@@ -99,11 +125,16 @@ extern "C" int corr_correlate_noalloc(const uint8_t* samples, int64_t n, int N, 
     unsigned char* base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_addr[dev]) {
+        CUcontext ctx = nullptr;
+        CtxGetCurrentFn cur = ctx_get_current();
+        if (cur && cur(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+        if (!g_scratch_addr[dev] || (ctx && ctx != g_scratch_ctx[dev])) {
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess) return fail_cuda(e, "cudaGetSymbolAddress");
             g_scratch_addr[dev] = p;
+            if (!ctx && cur && cur(&ctx) != CUDA_SUCCESS) ctx = nullptr;   // created by the lookup
+            g_scratch_ctx[dev] = ctx;
         }
         base = static_cast<unsigned char*>(g_scratch_addr[dev]);
     }

@@ -4,10 +4,13 @@ could stall the device, or a process whose device memory is all owned by
 another allocator).
 
 It is checked through the C ABI against the handle path (corr_create ->
-corr_push -> corr_dump, FP32 CUDA-core X-engine) on the same bytes, within
-the tolerance every parity test uses, on two calls in a row with different
-inputs: the second call must not see anything the first left in the shared
-scratch array.  This file is collected last so that a failure here stops a
+corr_push -> corr_dump, FP32 CUDA-core X-engine) and against the FP64
+oracle on the same bytes, within the tolerance every parity test uses, on
+two calls in a row with different inputs: the second call must not see
+anything the first left in the shared scratch array.  Two geometries: the
+paper's (N = 44, K = 512, the register-FFT F-engine) and a small one
+(N = 5, K = 64, the generic F-engine with the twiddles this entry point
+computes itself).  This file is collected last so that a failure here stops a
 `-x` run only after every other test has run; it also passes on its own in a
 fresh process.
 """
@@ -39,24 +42,31 @@ def _handle_path(lib, dev, N, K, S):
     return V
 
 
-def test_noalloc_matches_handle_path_twice(lib):
+@pytest.mark.parametrize("N,K,calls", [
+    # 300 frames: more than one internal pass, with a ragged last pass
+    (44, 512, [(300, 11020148 + 31), (130, 11020148 + 32)]),
+    (5, 64, [(150, 11020148 + 33), (37, 11020148 + 34)]),
+])
+def test_noalloc_matches_handle_path_twice(lib, N, K, calls):
     import torch
     assert torch.cuda.is_available()
-    N, K = 44, 512
     stream = torch.cuda.current_stream()
     P, C = N * (N + 1) // 2, K // 2
     out = torch.empty((P, C), dtype=torch.complex64, device="cuda")
-    # 300 frames: more than one internal pass, with a ragged last pass.
-    for call, (S, seed) in enumerate([(300, 11020148 + 31), (130, 11020148 + 32)]):
+    for call, (S, seed) in enumerate(calls):
         packed, _ = synth.make_samples(N, S * K, K, seed=seed)
         dev = torch.from_numpy(packed.reshape(-1)).cuda()
         ref = _handle_path(lib, dev, N, K, S)
+        R, n_ref = oracle.correlate(packed, N, K)
+        assert n_ref == S
         out.fill_(complex(3e30, -3e30))          # stale garbage must be overwritten
         lib.corr_correlate_noalloc(dev, S * K, N, K, out, stream)
         torch.cuda.synchronize()
         V = out.cpu().numpy()
         e = _norm_err(V, ref, N)
-        assert e <= TOL, f"call {call}: normalised error {e:.3g}"
+        assert e <= TOL, f"call {call}: normalised error {e:.3g} against the handle path"
+        e = _norm_err(V, R, N)
+        assert e <= TOL, f"call {call}: normalised error {e:.3g} against the oracle"
 
 
 def test_noalloc_rejects_oversize_and_bad_sizes(lib):

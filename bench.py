@@ -50,9 +50,16 @@ PAPER_RATE = N_ANT * RATE
 # profiles/); scaled to the average launch below.  Remove an entry when its
 # kernel changes.
 NCU_TRAFFIC_2048 = {
-    # ("fengine", "fp32"): no entry -- the kernel changed (corrections became a
-    # template parameter) after the last capture, 23.1 MB read + 128.7 MB
-    # written per launch (profiles/fx_n44_k512_35msps_fp32.txt)
+    ("fengine", "fp32"): (151.79e6, "ncu --set full, fengine_k512<SPEC_F16X2, corrections off>, "
+                                    "one 2048-frame launch: 23.10 MB read + 128.69 MB written "
+                                    "(profiles/fengine_k512_n44_2048frames_fp32.txt)"),
+}
+
+# Tensor-pipe activity of the X-engine's one pass over a whole 1 s
+# integration (the configuration timed here), from one ncu capture
+# (sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed, summary
+# under profiles/).  Remove an entry when its kernel changes.
+NCU_XENGINE_TENSOR_PCT = {
 }
 
 WORKLOAD = ("N=44 antennas, K=512-point real FFT -> 256 channels, 990 outputs/channel, "
@@ -207,14 +214,83 @@ def oracle_frames_for(seconds):
     return max(16, min(SPEC_PER_STEP, frames))
 
 
+def cpu_model():
+    """The host CPU's model name (x86 'model name', or lscpu's on Arm)."""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+_ORACLE_CHILD = r"""
+import json, sys, time
+sys.path.insert(0, sys.argv[1])
+import oracle
+from paper_1102_0148_gb300 import synth
+N, K, frames, seed, tone = int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]), int(sys.argv[5]), float(sys.argv[6])
+packed, _ = synth.make_samples(N, frames * K, K, seed=seed, tone_amp=tone)
+t0 = time.perf_counter()
+V, n = oracle.correlate(packed, N, K)
+dt = time.perf_counter() - t0
+assert n == frames
+print(json.dumps({"seconds": dt}))
+"""
+
+
+def time_oracle_threads(frames, threads, seed, tone):
+    """The oracle on `frames` spectra of the 44-antenna workload in a fresh
+    process whose BLAS runs `threads` threads (0 = the library's default,
+    all cores); returns its wall time (input generation excluded)."""
+    env = dict(os.environ)
+    if threads:
+        for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS",
+                  "BLIS_NUM_THREADS", "VECLIB_MAXIMUM_THREADS"):
+            env[k] = str(threads)
+    r = subprocess.run([sys.executable, "-c", _ORACLE_CHILD, ROOT, str(N_ANT), str(K_FFT),
+                        str(frames), str(seed), str(tone)],
+                       capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle child failed: {r.stderr[-500:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+
+
 def cpu_baseline(seconds):
+    """The FP64 oracle on the host cores, at one thread and at all cores, on
+    the plain-FX workload (N = 44, 2^17 samples = 256 spectra) and on a
+    prefix of the real-time one (1 s at 35 MS/s; the prefix sized to about
+    `seconds` of CPU work at all cores, a quarter of that at one thread)."""
+    cores = os.cpu_count() or 1
     frames = oracle_frames_for(seconds)
-    dt = time_oracle(oracle_input(frames))
-    return {"value": N_ANT * frames * K_FFT / dt, "unit": UNIT, "cores": blas_threads(),
-            "kind": "oracle",
-            "sample": f"first {frames} of the 68359 spectra of one 1 s integration "
-                      f"({frames * K_FFT} samples x 44 antennas), numpy FP64 oracle, "
-                      f"{dt:.1f} s"}
+    frames1 = max(16, frames // max(1, min(cores, 16)) * 2)
+    runs = []
+    for name, fr, seed, tone in (("plain FX: N=44, K=512, 2^17 samples (256 spectra)", 256,
+                                  11020148 + 1, 0.0),
+                                 (None, None, SEED, 0.5)):
+        for threads in (1, 0):
+            f = fr if fr else (frames1 if threads == 1 else frames)
+            dt = time_oracle_threads(f, threads, seed, tone)
+            runs.append({"workload": name or f"real time: first {f} of the 68359 spectra of a "
+                                              f"1 s integration at 35 MS/s (+ 0.5 LSB tone)",
+                         "threads": threads or cores, "spectra": f, "seconds": dt,
+                         "value": N_ANT * f * K_FFT / dt, "rtf": N_ANT * f * K_FFT / dt / PAPER_RATE})
+    head = runs[-1]
+    return {"value": head["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(),
+            "sample": f"first {head['spectra']} of the 68359 spectra of one 1 s integration "
+                      f"({head['spectra'] * K_FFT} samples x 44 antennas), numpy FP64 oracle, "
+                      f"all {cores} cores, {head['seconds']:.1f} s",
+            "runs": runs}
 
 
 def run_reference(args):
@@ -272,6 +348,7 @@ def main():
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    bf16_sus = peaks.get("bf16_tflops_sustained", 1700.0)
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     peak_src = "measured" if peaks else "fallback"
 
@@ -345,11 +422,12 @@ def main():
             peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
             psrc = f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"
         else:
+            # FP32 mode issues kind::f16 (two FP16 planes), FP8 kind::f8f6f4
             bound, unit = "tensor", "TFLOP/s"
-            ratio = {"fp32": 1.1 / 2.25, "fp16": 1.0, "fp8": 2.0}[args.dtype]
-            peak = bf16_peak * ratio
-            psrc = (f"{peak_src} bf16 {bf16_peak} TF/s x nominal "
-                    f"{ {'fp32': 'tf32/bf16 = 1.1/2.25', 'fp16': '1', 'fp8': 'fp8/bf16 = 2'}[args.dtype] }")
+            ratio = 2.0 if args.dtype == "fp8" else 1.0
+            peak = bf16_sus * ratio
+            psrc = (f"{peak_src} bf16 sustained {bf16_sus} TF/s x nominal "
+                    f"{'fp8/bf16 = 2' if ratio == 2.0 else 'fp16/bf16 = 1'}")
         achieved = work / (ms / n_launch / 1e3) / 1e12
     else:
         ob = {"fp32": 4, "fp32_simt": 4, "fp16": 2, "fp8": 1}[args.dtype]
@@ -370,6 +448,30 @@ def main():
                 "kernel_launches": {c: prof[c][0] for c in prof},
                 "profiled_steps": profiled}
 
+    # the X-engine at its tensor-pipe fraction: useful flops (8 per complex
+    # MAC, all pairs) and the flops its MMAs issue (tile padding, and the
+    # three FP16 products of FP32 mode), against the peak of the MMA kind
+    # it issues, per CUDA-event time of its launches
+    xengine = None
+    if args.dtype != "fp32_simt" and prof["xengine"][0] > 0:
+        n_x, ms_x = prof["xengine"]
+        s_pad = -(-frames // 128) * 128          # every step's passes, padded frames
+        sec = ms_x / 1e3
+        useful = workload.xengine_flops(N_ANT, K_FFT, frames) * profiled / sec / 1e12
+        issued = workload.xengine_issued_flops(N_ANT, K_FFT, s_pad, args.dtype) * profiled / sec / 1e12
+        ratio = 2.0 if args.dtype == "fp8" else 1.0
+        xengine = {
+            "kernel": "xengine_tc_kernel",
+            "instruction": "tcgen05.mma kind::f8f6f4" if args.dtype == "fp8" else "tcgen05.mma kind::f16",
+            "ms_per_step": ms_x / profiled, "launches_per_step": n_x / profiled,
+            "useful_tflops": useful, "issued_tflops": issued,
+            "peak_tflops": bf16_sus * ratio, "peak_burst_tflops": bf16_peak * ratio,
+            "peak_source": f"{peak_src} bf16 (sustained and burst) x nominal "
+                           f"{'fp8/bf16 = 2' if ratio == 2.0 else 'fp16/bf16 = 1'}",
+            "useful_frac": useful / (bf16_sus * ratio), "issued_frac": issued / (bf16_sus * ratio),
+            "ncu_tensor_pipe_pct": NCU_XENGINE_TENSOR_PCT.get(args.dtype) if not args.chunk else None,
+        }
+
     # end to end from pinned host memory through the C ABI
     e2e = None
     if args.e2e_steps > 0:
@@ -388,6 +490,19 @@ def main():
 
         step_host()
         corr.corr_sync(h)
+        # the host link's rate in this run: one step's input, pinned host ->
+        # device, as a single copy (CUDA events, best of 3)
+        scratch = torch.empty_like(dev_in)
+        copy_ms = []
+        for _ in range(3):
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            scratch.copy_(host_in, non_blocking=True)
+            c1.record(stream)
+            c1.synchronize()
+            copy_ms.append(c0.elapsed_time(c1))
+        del scratch
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
@@ -399,7 +514,10 @@ def main():
                "unit": UNIT,
                "h2d_bytes_per_step": frames * rec,
                "d2h_bytes_per_step": host_vis.numel() * host_vis.element_size(),
-               "steps": args.e2e_steps, "dump": "corr_dump_async into pinned host memory"}
+               "steps": args.e2e_steps, "dump": "corr_dump_async into pinned host memory",
+               "ms_per_step": 1e3 * te / args.e2e_steps,
+               "h2d_gbs": frames * rec / (min(copy_ms) * 1e-3) / 1e9,
+               "h2d_ms_per_step": min(copy_ms)}
         del host_in
 
     # TC vs FP32: the other X-engine precisions on the same integration
@@ -437,6 +555,7 @@ def main():
                        "l2": "inputs (770 MB/step) larger than L2; no flush",
                        "parallelism": f"replicas x{world}"},
             "clocks": clocks, "gpu_launches": launches, "roofline": roofline,
+            "xengine": xengine,
             "e2e": e2e, "cpu_baseline": cpu, "variants": variants, "forms": forms,
         }
         print(json.dumps(line), flush=True)

@@ -42,7 +42,9 @@ def test_bounded_wait_timeout_is_reported_and_recovered(lib, dtype):
         c.push(dev, S * K)                       # the handle is still usable
         V, n = c.dump(fp64=True)
     assert n == S
-    assert _err(V, R, N) <= (1e-5 if dtype == "fp32" else 1e-3)
+    from conftest import report_err
+    e = report_err(f"faults-resume-{dtype}", _err(V, R, N))
+    assert e <= (1e-5 if dtype == "fp32" else 2.2e-4)    # FP16: 1.1e-4 measured
 
 
 @pytest.mark.gpu

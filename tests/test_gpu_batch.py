@@ -94,7 +94,10 @@ def test_batch_fp16(lib):
         b.push(dev)
         vis, n = b.dump(fp64=True)
     for (N, K), V, R in zip(modes, vis, refs):
-        assert norm_err(V, R, N) <= 1e-3
+        from conftest import report_err
+        # about twice the measured 1.3e-4, 2.6e-4, 3.7e-4
+        bound = {512: 2.6e-4, 2048: 5.2e-4, 4096: 7.4e-4}[K]
+        assert report_err(f"batch-fp16-N{N}-K{K}", norm_err(V, R, N)) <= bound
 
 
 def test_batch_rejects_mixed_or_bad_arguments(lib):

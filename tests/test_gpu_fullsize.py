@@ -7,13 +7,15 @@ the same bytes at a sample of channels -- DC, the tone, and three others --
 for all 990 pairs.  The FP32 paths must stay within the 1e-5 normalised
 bound at this length too: the X-engine sums at most one work item (a few
 hundred spectra) in FP32 before the FP64 accumulation, so the FP32 error
-does not grow with the integration.  The FP16 / FP8 errors are stated.
+does not grow with the integration.  The FP16 / FP8 bounds are about twice
+the errors measured on a GB300 (5.9e-6 and 2.0e-3).
 """
 
 import numpy as np
 import pytest
 
 import oracle
+from conftest import report_err
 from paper_1102_0148_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -22,7 +24,7 @@ N, K, RATE = 44, 512, 35e6
 FRAMES = int(RATE // K)                   # 68359
 CHUNK = (1 << 20) // K                    # 2048 frames per push
 CHANNELS = [0, 1, 97, 170, 255]
-BOUND = {"fp32": 1e-5, "fp32_simt": 1e-5, "fp16": 1e-3, "fp8": 5e-2}
+BOUND = {"fp32": 1e-5, "fp32_simt": 1e-5, "fp16": 1.2e-5, "fp8": 4e-3}
 
 
 @pytest.fixture(scope="module")
@@ -54,5 +56,5 @@ def test_one_second_integration(lib, workload, dtype):
     nrm = np.sqrt(A[[p[0] for p in pairs]] * A[[p[1] for p in pairs]])
     e = np.abs(Vs - R) / nrm
     per_ch = {ch: float(e[:, m].max()) for m, ch in enumerate(CHANNELS)}
-    print(f"{dtype}: max normalised error per channel {per_ch}")
+    report_err(f"full1s-{dtype}", max(per_ch.values()))
     assert max(per_ch.values()) <= BOUND[dtype], per_ch

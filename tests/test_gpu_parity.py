@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 import oracle
+from conftest import report_err
 from paper_1102_0148_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -214,10 +215,15 @@ def test_profiler_counts_launches(lib, torch_cuda):
 
 
 # Precision forms: single-plane FP16 / FP8-E4M3 tensor-core inputs.  Stated
-# bounds on the normalised error against the FP64 oracle (cfg1 input):
-# FP16 carries 2^-11 relative rounding per element, ~1e-4 after 256
-# spectra; FP8-E4M3 carries 2^-4, ~1e-2.
-PRECISION_BOUND = {"fp16": 1e-3, "fp8": 5e-2}
+# bounds on the normalised error against the FP64 oracle, about twice the
+# error measured on a GB300 for the same seeded input (FP16 carries 2^-11
+# relative rounding per element, FP8-E4M3 2^-4):
+#   cfg1 (N = 44, K = 512, 256 spectra): FP16 1.3e-4, FP8 1.7e-2 measured;
+#   K = 2048 / 4096 with corrections: FP16 2.4e-4 / 3.2e-4, FP8 3.3e-2 /
+#   3.9e-2 measured (FP8 held to 5e-2, 1.3-1.5x).
+PRECISION_BOUND = {"fp16": 3e-4, "fp8": 4e-2}
+LARGE_K_BOUND = {("fp16", 2048): 5e-4, ("fp16", 4096): 7e-4, ("fp8", 2048): 5e-2,
+                 ("fp8", 4096): 5e-2}
 
 
 @pytest.mark.parametrize("dtype", ["fp16", "fp8"])
@@ -227,8 +233,7 @@ def test_precision_forms_cfg1(lib, torch_cuda, dtype):
     R, S = oracle.correlate(packed, N, K)
     V, n = run_gpu(lib, torch_cuda, packed, N, K, dtype)
     assert n == S
-    e = vis_error(V, R, N)
-    print(f"{dtype}: normalised error vs FP64 oracle {e:.3g}")
+    e = report_err(f"cfg1-{dtype}", vis_error(V, R, N))
     assert e <= PRECISION_BOUND[dtype], e
 
 
@@ -270,8 +275,8 @@ def test_large_k_every_workspace_type(lib, torch_cuda, dtype, N, K, S):
                             delays=t32.astype(np.float64))
     V, n = run_gpu(lib, torch_cuda, packed, N, K, dtype, gains=g32, delays=t32)
     assert n == S
-    e = vis_error(V, R, N)
-    assert e <= PRECISION_BOUND.get(dtype, TOL), e
+    e = report_err(f"largek-{dtype}-N{N}-K{K}", vis_error(V, R, N))
+    assert e <= LARGE_K_BOUND.get((dtype, K), TOL), e
 
 
 def test_host_pushes_across_chunk_changes(lib, torch_cuda):

@@ -3,9 +3,12 @@ per-antenna, per-channel scaling from the autocorrelations, FP32
 accumulation (Sec. 4: float output converted to a narrower type with
 prescaling before the cross-multiply).
 
-Stated errors, normalised by sqrt(|V_ii V_jj|) against the FP64 oracle:
-  FP16 (11 significant bits): <= 1e-3 on a 2^20-sample prefix (2048 spectra);
-  FP8-E4M3 (4 significant bits): <= 5e-2.
+Stated errors, normalised by sqrt(|V_ii V_jj|) against the FP64 oracle on a
+2^20-sample prefix (2048 spectra), about twice the error measured on a GB300
+for this seeded input:
+  FP16 (11 significant bits): <= 1e-4 (4.9e-5 measured);
+  FP8-E4M3 (4 significant bits): <= 1.4e-2 (7.0e-3 measured).
+A 6 LSB tone with automatic scales: FP8 <= 5e-2 (2.5e-2 measured).
 The workload is the full-band one: N = 44, 80 MS/s, K = 512, 4-bit, with the
 oracle run on the first 2^20 samples per antenna.
 """
@@ -14,12 +17,14 @@ import numpy as np
 import pytest
 
 import oracle
+from conftest import report_err
 from paper_1102_0148_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
 N, K = 44, 512
-BOUND = {"fp16": 1e-3, "fp8": 5e-2}
+BOUND = {"fp16": 1e-4, "fp8": 1.4e-2}
+TONE_BOUND_FP8 = 5e-2
 
 
 def norm_err(V, R, N):
@@ -53,8 +58,7 @@ def prefix():
 def test_full_band_prefix_error(lib, prefix, dtype):
     dev, R, S = prefix
     V = correlate(lib, dev, S, dtype)
-    e = norm_err(V, R, N)
-    print(f"{dtype}: normalised error vs FP64 oracle on the 2^20-sample prefix: {e:.3g}")
+    e = report_err(f"prefix80-{dtype}", norm_err(V, R, N))
     assert e <= BOUND[dtype]
 
 
@@ -70,8 +74,9 @@ def test_scaling_prevents_fp8_saturation(lib):
     e_auto = norm_err(correlate(lib, dev, S, "fp8"), R, N)
     ones = np.ones((N, K // 2), np.float32)
     e_unit = norm_err(correlate(lib, dev, S, "fp8", scales=ones), R, N)
-    print(f"fp8 strong tone: auto scales {e_auto:.3g}, unit scales {e_unit:.3g}")
-    assert e_auto <= BOUND["fp8"]
+    report_err("fp8-tone6-auto", e_auto)
+    report_err("fp8-tone6-unit", e_unit)
+    assert e_auto <= TONE_BOUND_FP8
     assert e_unit > 10 * e_auto
 
 
@@ -98,7 +103,7 @@ def test_user_scales_do_not_bias(lib, prefix):
     rng = np.random.default_rng(0)
     sc = (2.0 ** rng.integers(-3, 4, (N, K // 2))).astype(np.float32) * 16
     V = correlate(lib, dev, S, "fp16", scales=sc)
-    assert norm_err(V, R, N) <= BOUND["fp16"]
+    assert report_err("prefix80-fp16-user-scales", norm_err(V, R, N)) <= BOUND["fp16"]
 
 
 def test_scales_rejected_on_fp32_handles(lib):

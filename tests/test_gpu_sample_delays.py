@@ -53,7 +53,9 @@ def test_delayed_stream_matches_oracle(lib, torch, dtype, K, host):
             f0 += nf
         V, n = c.dump(fp64=True)
     assert n == F
-    assert vis_error(V, R, N) <= (TOL if dtype != "fp16" else 1e-3)
+    from conftest import report_err
+    e = report_err(f"sdelay-{dtype}-K{K}-host{int(host)}", vis_error(V, R, N))
+    assert e <= (TOL if dtype != "fp16" else 2e-4)      # FP16: 0.8e-4 .. 0.9e-4 measured
 
 
 def test_delays_change_mid_stream_and_persist_across_dumps(lib, torch):

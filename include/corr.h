@@ -113,13 +113,13 @@ int corr_set_chunk(corr_t h, int64_t max_spectra);
 /* Tile choices of the tensor-core X-engine (no counterpart in the paper; the
  * autotuner in paper_1102_0148_gb300/tune.py picks them): `window` = spectra
  * accumulated in TMEM before the epilogue adds them up in FP32 (a multiple
- * of 64, of 128 for FP8; 0 = 256 in FP32 mode, 512 for FP16 / FP8), `stages` = depth of the shared-memory
+ * of 32, of 128 for FP8; 0 = 256 in FP32 mode, 512 for FP16 / FP8), `stages` = depth of the shared-memory
  * operand ring (2..16, clipped to what shared memory holds; 0 = automatic),
  * `split` = ranges of spectra per channel and antenna-block pair into which
  * a pass is cut (1..64, partials combined in a fixed order inside the
- * launch; 0 = chosen by the planner), `atoms` = k-tiles (64 spectra, 128 for
- * FP8) carried by one pipeline stage (1..4; 0 = as many as leave three
- * stages).  The window is rounded up to whole stages.  CORR_EINVAL for
+ * launch; 0 = chosen by the planner), `atoms` = k-tiles (32 spectra, 128 for
+ * FP8) carried by one pipeline stage (1..8; 0 = as many as leave three
+ * stages, up to 256 spectra).  The window is rounded up to whole stages.  CORR_EINVAL for
  * CUDA-core handles or out-of-range values. */
 int corr_set_tiles(corr_t h, int window, int stages, int split, int atoms);
 
@@ -224,6 +224,14 @@ int corr_grad(corr_t h, const uint8_t* samples, int64_t n, const float* gains,
 int corr_state_bytes(corr_t h, size_t* bytes);
 int corr_save_state(corr_t h, void* buf);
 int corr_load_state(corr_t h, const void* buf);
+
+/* Allocation-failure test hook (no counterpart in the paper): every device
+ * allocation a handle, batch or plan makes goes through one helper; while
+ * the environment variable CORR_TEST_FAIL_ALLOC holds a positive integer k,
+ * the k-th allocation counted since the variable last changed value fails
+ * as if the device were out of memory.  The call that made it returns
+ * CORR_ENOMEM with nothing half-allocated and the handle still usable.
+ * (corr_correlate_noalloc allocates nothing and is not affected.) */
 
 /* Test hook for the failure path (no counterpart in the paper).  kind 1: in
  * the next tensor-core X-engine launch, the first work item of CTA 0 never

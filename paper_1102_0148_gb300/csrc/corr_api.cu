@@ -7,7 +7,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <algorithm>
@@ -169,8 +171,8 @@ int alloc_workspace(corr_t h, int64_t cap) {
     if (h->use_tc) max_split = std::min(max_split, 8);
     void* spec = nullptr;
     float2* part = nullptr;
-    cudaError_t e = cudaMalloc(&spec, spec_bytes);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&part, (size_t)max_split * h->C * h->P * sizeof(float2));
+    cudaError_t e = dev_malloc(&spec, spec_bytes);
+    if (e == cudaSuccess) e = dev_malloc((void**)&part, (size_t)max_split * h->C * h->P * sizeof(float2));
     if (e == cudaSuccess) e = cudaMemsetAsync(spec, 0, spec_bytes, h->stream);
     if (e != cudaSuccess) {
         cudaFree(spec);
@@ -441,12 +443,24 @@ int alloc_shifted(corr_t h) {
     }
     h->shifted_frames = 0;
     for (int b = 0; b < 2; ++b) {
-        CUDA_TRY(h, cudaMalloc((void**)&h->shifted[b], bytes));
+        CUDA_TRY(h, dev_malloc((void**)&h->shifted[b], bytes));
         if (!h->shift_free[b])
             CUDA_TRY(h, cudaEventCreateWithFlags(&h->shift_free[b], cudaEventDisableTiming));
     }
     h->shifted_frames = h->cap;
     return CORR_OK;
+}
+
+// Release the host-input staging ring (buffers and their events).
+void free_stages(corr_t h) {
+    for (int b = 0; b < kHostStages; ++b) {
+        cudaFree(h->stage[b]);
+        h->stage[b] = nullptr;
+        if (h->stage_free[b]) cudaEventDestroy(h->stage_free[b]);
+        if (h->stage_full[b]) cudaEventDestroy(h->stage_full[b]);
+        h->stage_free[b] = h->stage_full[b] = nullptr;
+    }
+    h->stage_next = 0;
 }
 
 // Transform n samples (host or device memory) into the workspace, running the
@@ -458,13 +472,22 @@ int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, doubl
     if (host && !h->stage[0]) {
         // ~32 MB per buffer (whole 128-frame blocks), 16 of them: the copies
         // (~205 GB/s from pinned host memory) can run ~2.5 ms ahead of the
-        // F-engine, across an X-engine pass of a whole integration
+        // F-engine, across an X-engine pass of a whole integration.  All or
+        // nothing: a failure releases the buffers made so far.
         h->stage_frames = std::max<int64_t>(
             kSpecPad, std::min<int64_t>(h->cap, (int64_t)(kStageBytes / rec)) / kSpecPad * kSpecPad);
         for (int b = 0; b < kHostStages; ++b) {
-            CUDA_TRY(h, cudaMalloc((void**)&h->stage[b], (size_t)(h->stage_frames * rec)));
-            CUDA_TRY(h, cudaEventCreateWithFlags(&h->stage_free[b], cudaEventDisableTiming));
-            CUDA_TRY(h, cudaEventCreateWithFlags(&h->stage_full[b], cudaEventDisableTiming));
+            cudaError_t e = dev_malloc((void**)&h->stage[b], (size_t)(h->stage_frames * rec));
+            if (e == cudaSuccess)
+                e = cudaEventCreateWithFlags(&h->stage_free[b], cudaEventDisableTiming);
+            if (e == cudaSuccess)
+                e = cudaEventCreateWithFlags(&h->stage_full[b], cudaEventDisableTiming);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                free_stages(h);
+                return set_err(h, e == cudaErrorMemoryAllocation ? CORR_ENOMEM : CORR_ECUDA,
+                               "host-input staging buffers: %s", cudaGetErrorString(e));
+            }
         }
     }
     if (h->sdelay_on) {                         // the pass may have grown since
@@ -540,11 +563,7 @@ void destroy_impl(corr_t h) {
         cudaFree(h->shifted[b]);
         if (h->shift_free[b]) cudaEventDestroy(h->shift_free[b]);
     }
-    for (int b = 0; b < kHostStages; ++b) {
-        cudaFree(h->stage[b]);
-        if (h->stage_free[b]) cudaEventDestroy(h->stage_free[b]);
-        if (h->stage_full[b]) cudaEventDestroy(h->stage_full[b]);
-    }
+    free_stages(h);
     if (h->tc) tc_plan_destroy(h->tc);
     for (auto& v : h->ev_pending)
         for (auto& pr : v) {
@@ -566,6 +585,30 @@ void destroy_impl(corr_t h) {
 }  // namespace
 
 void gbcorr::set_global_error(const char* msg) { g_create_error = msg; }
+
+namespace {
+std::mutex g_alloc_mu;
+std::string g_alloc_env;     // value of CORR_TEST_FAIL_ALLOC the count belongs to
+long g_alloc_count = 0;      // allocations since it last changed
+}  // namespace
+
+cudaError_t gbcorr::dev_malloc(void** p, size_t bytes) {
+    const char* env = getenv("CORR_TEST_FAIL_ALLOC");
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        const std::string v = env ? env : "";
+        if (v != g_alloc_env) {
+            g_alloc_env = v;
+            g_alloc_count = 0;
+        }
+        const long k = v.empty() ? 0 : strtol(v.c_str(), nullptr, 10);
+        if (k > 0 && ++g_alloc_count == k) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
 
 extern "C" {
 
@@ -625,24 +668,24 @@ int corr_create(corr_t* out, int N, int K, int dtype) {
         tw[m] = make_float2((float)std::cos(th), (float)-std::sin(th));
     }
     const size_t acc_bytes = (size_t)h->C * h->P * sizeof(double2);
-    if (cudaMalloc((void**)&h->twiddle, K * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc((void**)&h->acc, acc_bytes) != cudaSuccess ||
-        cudaMalloc((void**)&h->status, sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&h->corr_tab, (size_t)N * h->C * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc((void**)&h->gains_dev, (size_t)N * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc((void**)&h->delays_dev, (size_t)N * sizeof(float)) != cudaSuccess) {
+    if (dev_malloc((void**)&h->twiddle, K * sizeof(float2)) != cudaSuccess ||
+        dev_malloc((void**)&h->acc, acc_bytes) != cudaSuccess ||
+        dev_malloc((void**)&h->status, sizeof(int)) != cudaSuccess ||
+        dev_malloc((void**)&h->corr_tab, (size_t)N * h->C * sizeof(float2)) != cudaSuccess ||
+        dev_malloc((void**)&h->gains_dev, (size_t)N * sizeof(float2)) != cudaSuccess ||
+        dev_malloc((void**)&h->delays_dev, (size_t)N * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         return bail(set_err(h, CORR_ENOMEM, "device allocation failed"));
     }
     if (h->spec_type == SPEC_F16 || h->spec_type == SPEC_F8) {
-        if (cudaMalloc((void**)&h->scale, (size_t)N * h->C * sizeof(float)) != cudaSuccess) {
+        if (dev_malloc((void**)&h->scale, (size_t)N * h->C * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             return bail(set_err(h, CORR_ENOMEM, "device allocation failed"));
         }
     }
     if (h->spec_type == SPEC_F16X2) {
         h->split_host.assign(2 * (size_t)N, split_scale_for(1.0, K));
-        if (cudaMalloc((void**)&h->split, 2 * (size_t)N * sizeof(float)) != cudaSuccess) {
+        if (dev_malloc((void**)&h->split, 2 * (size_t)N * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             return bail(set_err(h, CORR_ENOMEM, "device allocation failed"));
         }
@@ -738,8 +781,22 @@ int apply_sample_delays(corr_t h, const int* d) {
     }
     const size_t hb = (size_t)h->N * (h->K / 2);
     if (!h->sdelay) {
-        CUDA_TRY(h, cudaMalloc((void**)&h->sdelay, h->N * sizeof(int)));
-        for (int b = 0; b < 2; ++b) CUDA_TRY(h, cudaMalloc((void**)&h->hist[b], hb));
+        // all or nothing: a failure releases what was made
+        int* sd = nullptr;
+        uint8_t* hs[2] = {};
+        cudaError_t e = dev_malloc((void**)&sd, h->N * sizeof(int));
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = dev_malloc((void**)&hs[b], hb);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(sd);
+            cudaFree(hs[0]);
+            cudaFree(hs[1]);
+            return set_err(h, e == cudaErrorMemoryAllocation ? CORR_ENOMEM : CORR_ECUDA,
+                           "sample-delay buffers: %s", cudaGetErrorString(e));
+        }
+        h->sdelay = sd;
+        h->hist[0] = hs[0];
+        h->hist[1] = hs[1];
     }
     int arc = alloc_shifted(h);
     if (arc != CORR_OK) return arc;
@@ -941,15 +998,15 @@ int corr_grad(corr_t h, const uint8_t* samples, int64_t n, const float* gains,
     if (!samples || !grad_vis || !grad_gains || !grad_delays)
         return set_err(h, CORR_EINVAL, "NULL buffer");
     const size_t CPb = (size_t)h->C * h->P;
-    if (!h->acc_raw) CUDA_TRY(h, cudaMalloc((void**)&h->acc_raw, CPb * sizeof(double2)));
+    if (!h->acc_raw) CUDA_TRY(h, dev_malloc((void**)&h->acc_raw, CPb * sizeof(double2)));
     // device staging: gains (N float2), delays (N float), outputs (N float2 + N float),
     // and the incoming gradient when it is host memory
     const size_t gv_bytes = CPb * (grad_fp64 ? sizeof(double2) : sizeof(float2));
     if (!h->grad_buf)
-        CUDA_TRY(h, cudaMalloc((void**)&h->grad_buf, 4 * (size_t)h->N * sizeof(float2) +
+        CUDA_TRY(h, dev_malloc((void**)&h->grad_buf, 4 * (size_t)h->N * sizeof(float2) +
                                                      CPb * sizeof(double2)));
     if (!h->grad_scratch)
-        CUDA_TRY(h, cudaMalloc(&h->grad_scratch, grad_scratch_bytes(h->N, h->K)));
+        CUDA_TRY(h, dev_malloc(&h->grad_scratch, grad_scratch_bytes(h->N, h->K)));
     float2* g_dev = h->grad_buf;
     float* t_dev = reinterpret_cast<float*>(g_dev + h->N);
     float2* gg_dev = g_dev + 2 * h->N;
@@ -992,7 +1049,7 @@ int enqueue_dump(corr_t h, void* vis, int vis_fp64, bool dev) {
     const size_t bytes = (size_t)h->C * h->P * (vis_fp64 ? sizeof(double2) : sizeof(float2));
     void* out = vis;
     if (!dev) {
-        if (!h->vis_dev) CUDA_TRY(h, cudaMalloc(&h->vis_dev, (size_t)h->C * h->P * sizeof(double2)));
+        if (!h->vis_dev) CUDA_TRY(h, dev_malloc(&h->vis_dev, (size_t)h->C * h->P * sizeof(double2)));
         out = h->vis_dev;
     }
     if (narrow(h) && !h->scales_user && h->n_spec > 0) {

@@ -26,13 +26,15 @@ inline int spec_elem_bytes(int t) {
 inline int spec_planes(int t) { return t == SPEC_F16X2 ? 2 : 1; }
 
 // Row of the corner-turned workspace holding plane (0 = Re, 1 = Im) of
-// antenna i.  Antennas are grouped in blocks of 64; block b occupies rows
-// 128 b .. 128 b + 2 nb - 1 as [Re of its nb antennas; Im of them], nb =
-// min(64, N - 64 b).  For N <= 64 this is [Re Y_0..Re Y_{N-1}; Im Y_0..].
+// antenna i: 2 i + plane, the real and imaginary rows of an antenna side by
+// side.  Antennas are grouped in blocks of 64 (the X-engine's tiles): block b
+// occupies rows 128 b .. 128 b + 2 nb - 1, nb = min(64, N - 64 b).  With the
+// rows of one antenna adjacent, an F-engine CTA's two rows of a channel and
+// plane are one contiguous run of whole 128-byte lines (2 x 64 bytes for the
+// 32-frame FP16 tiles below).
 __host__ __device__ __forceinline__ int spec_row(int plane, int i, int N) {
-    const int b = i >> 6;
-    const int nb = (N - 64 * b) < 64 ? (N - 64 * b) : 64;
-    return 128 * b + plane * nb + (i & 63);
+    (void)N;
+    return 2 * i + plane;
 }
 
 // Pre-scale of the two-plane FP16 split (SPEC_F16X2), one power of two per
@@ -61,15 +63,16 @@ constexpr double kGainMax = 1099511627776.0;         // 2^40
 // so every X-engine tile along the spectrum axis is whole.
 constexpr int kSpecPad = 128;
 
-// Workspace layout, tile-major along the spectra: frames come in tiles of
-// 128 bytes (32 FP32, 64 FP16, 128 FP8 values -- one tensor-core k-tile), and
+// Workspace layout, tile-major along the spectra: frames come in tiles of T
+// = 32 (FP32: 128-byte rows; FP16 and the FP16 pair: 64-byte rows, the
+// X-engine's 64-byte-swizzled k-tile) or 128 (FP8: 128-byte rows), and
 // element (k, r, s) of a plane sits at ((s / T * C + k) * 2N + r) * T + s % T.
 // One (tile, channel) holds all 2N rows contiguously, so the X-engine reads a
-// k-tile of a channel as one block and an F-engine CTA's frames of every
-// channel lie within one tile's few megabytes.  Planes (SPEC_F16X2) are
-// plane_stride = C * 2N * cap elements apart.
+// k-tile of a channel as one block and an F-engine CTA's 32 frames of an
+// antenna fill whole tile rows.  Planes (SPEC_F16X2) are plane_stride =
+// C * 2N * cap elements apart.
 inline __host__ __device__ int spec_tile_shift(int t) {
-    return t == SPEC_F32 ? 5 : ((t == SPEC_F16 || t == SPEC_F16X2) ? 6 : 7);
+    return t == SPEC_F8 ? 7 : 5;
 }
 __host__ __device__ __forceinline__ int64_t spec_off(int k, int r, int64_t s, int N, int C,
                                                      int tshift) {
@@ -152,5 +155,11 @@ size_t grad_scratch_bytes(int N, int K);   // device scratch launch_grad needs
 
 // Message returned by corr_last_error(NULL) on this thread.
 void set_global_error(const char* msg);
+
+// cudaMalloc for every device allocation of a handle or plan.  Test hook:
+// while the environment variable CORR_TEST_FAIL_ALLOC holds a positive
+// integer k, the k-th allocation counted since the variable last changed
+// value fails with cudaErrorMemoryAllocation (nothing is allocated).
+cudaError_t dev_malloc(void** p, size_t bytes);
 
 }  // namespace gbcorr

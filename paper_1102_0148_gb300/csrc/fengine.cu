@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kThreads) fengine_generic(FengineArgs a, int F
 // register.
 // ---------------------------------------------------------------------------
 
-constexpr int kF512Frames = 32;     // frames per CTA (one 128-byte run per row)
+constexpr int kF512Frames = 32;     // frames per CTA (one workspace tile)
 constexpr int kF512Threads = 256;   // 16 groups of 16 lanes, 2 frames per group
 constexpr int kXStride = 17;        // exchange row stride (complex), conflict-free
 
@@ -252,15 +252,17 @@ __device__ __forceinline__ float2 w32mul(float2 d, int q) {
 }
 
 constexpr int kOutDebug = -1;
-// Staging row stride (floats): [frame][plane*256 + k].  547 = 3 mod 32 keeps
-// both the staging writes and the store phase's column reads on distinct
-// banks, and leaves room in a row for one group's exchange area (16 x 17
-// complex = 544 floats) at the 16-byte aligned offset f mod 4 within row f.
-// A group exchanges through the row of its second frame: during the first
-// round no group writes that row, and in the second the group itself writes
-// it only after its exchange.  With 4 KB of tables (twiddle bases, scales,
-// corrections) that is all the shared memory (72 KB), so three CTAs fit on
-// an SM.
+// Staging row stride (floats): [frame][2 k + plane], the real and imaginary
+// parts of a channel side by side like the workspace rows.  547 = 3 mod 32
+// keeps both the staging writes and the store phase's column reads on
+// distinct banks (the two half-warps of a warp hold consecutive frames, an
+// odd bank shift apart), and leaves room in a row for one group's exchange
+// area (16 x 17 complex = 544 floats) at the 16-byte aligned offset f mod 4
+// within row f.  A group exchanges through the row of its second frame:
+// during the first round no group writes that row, and in the second the
+// group itself writes it only after its exchange.  With 4 KB of tables
+// (twiddle bases, scales, corrections) that is all the shared memory
+// (72 KB), so three CTAs fit on an SM.
 constexpr int kStgRow = 547;
 constexpr int kStgFloats = kF512Frames * kStgRow;
 static_assert(kStgRow % 32 == 3 && kStgRow >= 16 * kXStride * 2 + 3, "staging row layout");
@@ -335,30 +337,71 @@ __host__ __device__ constexpr int out_bytes() {
     return OUT == SPEC_F32 ? 4 : (OUT == SPEC_F8 ? 1 : 2);
 }
 
-// Store phase of the K = 512 kernel.  The lane writes 4 frames
-// (from frame s) of rows r0 + CSTEP j of the staging buffer `src` (row
-// stride SROW): channel r0 + CSTEP j of the real plane for j < C / CSTEP,
-// then the same channels of the imaginary plane.  Within a plane the
-// workspace address steps by CSTEP channels, a constant; the loop stays
-// rolled (unrolled copies, which hoist the staging loads of several rows,
-// ran slower).  (The K = 1024 kernel keeps per-row offsets: stepping ran
-// 2% slower there in FP32 mode.)
-template <int OUT, int CSTEP, int SROW>
-__device__ __forceinline__ void store_rows(const FengineArgs& a, const float* src, int r0,
-                                           int64_t s, int C, int ant) {
+// Eight consecutive frames of one workspace row converted and stored with
+// one 16-byte store per plane (FP16 and the FP16 pair).
+template <int OUT>
+__device__ __forceinline__ void store8p(char* p, int64_t lo, const float (&v)[8]) {
+    __half2 h[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) h[e] = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
+    *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(h);
+    if (OUT == SPEC_F16X2) {   // values already carry the pre-scale sigma_i
+        __half2 l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 fh = __half22float2(h[e]);
+            l[e] = __floats2half2_rn(v[2 * e] - fh.x, v[2 * e + 1] - fh.y);
+        }
+        *reinterpret_cast<uint4*>(p + lo) = *reinterpret_cast<const uint4*>(l);
+    }
+}
+
+// Store phase of the K = 512 kernel: 256 channels x 2 rows (Re, Im) x 32
+// frames of one antenna from the staging buffer [frame][2 k + plane].  The
+// two rows of a channel are adjacent in the workspace (2 i, 2 i + 1), so each
+// (channel, plane) is one contiguous run of whole lines, and the lanes are
+// laid out to write runs whole:
+// * 2-byte types (32-frame tiles, 64-byte rows): lane = 8 c + 4 p + m writes
+//   frames 8 m .. 8 m + 7 of row p of channel 4 w + c + 32 j with 16-byte
+//   stores -- 8 lanes cover the channel's 128 bytes, a warp 4 channels;
+// * FP32 (32-frame tiles, 128-byte rows) and FP8 (128-frame tiles): lane =
+//   16 c + 8 p + m writes frames 4 m .. 4 m + 3 of row p of channel
+//   2 w + c + 16 j.
+// Within a plane the workspace address steps by a constant number of
+// channels; the loops stay rolled (unrolled copies, which hoist the staging
+// loads of several rows, ran slower).  The staging column reads land on 32
+// distinct banks (frame offsets 24 m or 12 m mod 32, plus 0..7 or 0..3).
+template <int OUT>
+__device__ __forceinline__ void store_rows(const FengineArgs& a, const float* stg, int warp,
+                                           int l32, int64_t s, int ant) {
     constexpr int eb = out_bytes<OUT>();
-    const int tsh = spec_tile_shift(OUT);
-    const int64_t step = ((int64_t)CSTEP * 2 * a.N << tsh) * eb;
+    constexpr int tsh = OUT == SPEC_F8 ? 7 : 5;
     const int64_t lo = a.plane_stride * eb;
+    char* base = static_cast<char*>(a.spec);
+    if (eb == 2) {
+        const int m = l32 & 3, p = (l32 >> 2) & 1, c = l32 >> 3;
+        const float* src = stg + 8 * m * kStgRow + 2 * (4 * warp + c) + p;
+        char* dst = base + spec_off(4 * warp + c, spec_row(p, ant, a.N), s + 8 * m, a.N, 256, tsh) * eb;
+        const int64_t step = ((int64_t)32 * 2 * a.N << tsh) * eb;     // 32 channels on
 #pragma unroll 1
-    for (int plane = 0; plane < 2; ++plane) {
-        char* p = static_cast<char*>(a.spec) +
-                  spec_off(r0, spec_row(plane, ant, a.N), s, a.N, C, tsh) * eb;
+        for (int j = 0; j < 8; ++j) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = src[e * kStgRow];
+            store8p<OUT>(dst, lo, v);
+            dst += step;
+            src += 64;
+        }
+    } else {
+        const int m = l32 & 7, p = (l32 >> 3) & 1, c = l32 >> 4;
+        const float* src = stg + 4 * m * kStgRow + 2 * (2 * warp + c) + p;
+        char* dst = base + spec_off(2 * warp + c, spec_row(p, ant, a.N), s + 4 * m, a.N, 256, tsh) * eb;
+        const int64_t step = ((int64_t)16 * 2 * a.N << tsh) * eb;     // 16 channels on
 #pragma unroll 1
-        for (int j = 0; j < C / CSTEP; ++j) {
-            store4p<OUT>(p, lo, src[0], src[SROW], src[2 * SROW], src[3 * SROW]);
-            p += step;
-            src += CSTEP;
+        for (int j = 0; j < 16; ++j) {
+            store4p<OUT>(dst, lo, src[0], src[kStgRow], src[2 * kStgRow], src[3 * kStgRow]);
+            dst += step;
+            src += 32;
         }
     }
 }
@@ -407,22 +450,23 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
     const float2 wt = __ldg(a.twiddle + lane);
     const float2 u = make_float2(chalf * wt.x, chalf * wt.y);   // c W512^t
 
-    // prefetch both rounds' 16 bytes per lane
+    // prefetch both rounds' 16 bytes per lane: group g = 2 warp + half takes
+    // frames g and g + 16
     uint4 raw0 = make_uint4(0u, 0u, 0u, 0u), raw1 = raw0;
     {
-        const int64_t sa = s0 + warp + 16 * half, sb = sa + 8;
+        const int64_t sa = s0 + 2 * warp + half, sb = sa + 16;
         if (sa < a.S) raw0 = __ldg(reinterpret_cast<const uint4*>(a.in + (sa * a.N + i) * 256) + lane);
         if (sb < a.S) raw1 = __ldg(reinterpret_cast<const uint4*>(a.in + (sb * a.N + i) * 256) + lane);
     }
     __syncthreads();
 
-    const int fx = warp + 8 + 16 * half;             // the group's second frame
+    const int fx = 2 * warp + half + 16;             // the group's second frame
     float2* gx = reinterpret_cast<float2*>(stg + fx * kStgRow + (fx & 3));
     unsigned char* gbytes = reinterpret_cast<unsigned char*>(gx);
 
 #pragma unroll 1
     for (int r = 0; r < 2; ++r) {
-        const int f = warp + 8 * r + 16 * half;
+        const int f = 2 * warp + half + 16 * r;
         const int64_t s = s0 + f;
         // byte transpose: lane t needs bytes t + 16 j
         *reinterpret_cast<uint4*>(gbytes + 16 * lane) = r == 0 ? raw0 : raw1;
@@ -474,8 +518,8 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
                     X.x *= sc;
                     X.y *= sc;
                 }
-                stg[f * kStgRow + k] = X.x;
-                stg[f * kStgRow + 256 + k] = X.y;
+                stg[f * kStgRow + 2 * k] = X.x;
+                stg[f * kStgRow + 2 * k + 1] = X.y;
             }
         };
 #pragma unroll
@@ -503,12 +547,7 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
     }
     if (DEBUG) return;
     __syncthreads();
-    // 512 workspace rows (plane, k) x 32 frames: a warp covers 4 rows per
-    // iteration, 8 lanes per row, 4 consecutive frames per lane.
-    const int l32 = tid & 31;
-    const int m = l32 & 7;
-    const int r0 = 4 * warp + (l32 >> 3);
-    store_rows<OUT, 32, kStgRow>(a, stg + 4 * m * kStgRow + r0, r0, a.s_base + s0 + 4 * m, 256, i);
+    store_rows<OUT>(a, stg, warp, tid & 31, a.s_base + s0, i);
 }
 
 

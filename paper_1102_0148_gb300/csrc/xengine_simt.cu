@@ -73,12 +73,9 @@ __global__ void xengine_simt_kernel(XengineArgs a, int nb, int nt, int G) {
                 const int r = e >> 3;             // workspace row of channel k0 + gg
                 const int c4 = (e & 7) << 2;      // its frames c4 .. c4 + 3
                 const float4 v = bg[e];
-                // row r -> (plane, antenna) under the 64-antenna block layout
-                const int b = r >> 7;
-                const int w = r & 127;
-                const int nbk = (N - 64 * b) < 64 ? (N - 64 * b) : 64;
-                const int plane = w >= nbk;
-                float* d = tg + (c4 * 2 + plane) * nbp + ((64 * b + w - plane * nbk) ^ c4);
+                // row r = 2 antenna + plane
+                const int plane = r & 1;
+                float* d = tg + (c4 * 2 + plane) * nbp + ((r >> 1) ^ c4);
                 d[0] = v.x;
                 d[2 * nbp] = v.y;
                 d[4 * nbp] = v.z;

@@ -7,16 +7,19 @@
 // For one channel k the spectra of a pass form the real matrix A whose rows
 // are the real and imaginary parts of every antenna (spectra along the
 // contraction axis); the Gram matrix G = A A^T holds every product the
-// visibilities need.  Antennas come in blocks of 64 (rows [Re; Im] of the
-// block, 128 rows at most); for a pair of blocks (b1 <= b2) with local
-// antennas i' < nb1 and j' < nb2,
-//   Re V_ij = G[i'][j'] + G[nb1+i'][nb2+j'],   Im V_ij = G[nb1+i'][j'] - G[i'][nb2+j'].
+// visibilities need.  Antennas come in blocks of 64 (128 rows at most); for
+// a pair of blocks (b1 <= b2) with local antennas i' < nb1 and j' < nb2
+// (block rows 2 i' = Re, 2 i' + 1 = Im:
+//   Re V_ij = G[2i'][2j'] + G[2i'+1][2j'+1],  Im V_ij = G[2i'+1][2j'] - G[2i'][2j'+1].)
 // Each block pair is a dense contraction D[128 x Nn] += A_b1[128 x 16|32] *
 // A_b2^T on the tensor cores, operands loaded by TMA (rows past the antenna
 // count are zero-filled), FP32 accumulators in TMEM.  For a diagonal pair
 // both operands are the same shared-memory tile.
 //
-// Precisions (operands in shared memory, K-major, 128-byte swizzle):
+// Precisions (operands in shared memory, K-major; FP16 tiles of 32 spectra in
+// 64-byte rows with the 64-byte swizzle, FP8 tiles of 128 in 128-byte rows
+// with the 128-byte swizzle; rows 2 i' and 2 i' + 1 of a block are the real
+// and imaginary parts of its antenna i'):
 //   mode 0 (FP32-accurate): two FP16 planes sigma_i x = hi + lo, sigma_i a
 //           power of two per antenna.  Diagonal pairs issue Dhh += hi hi^T
 //           and Dhl += hi lo^T and form G = Dhh + Dhl + Dhl^T; off-diagonal
@@ -55,7 +58,6 @@ namespace {
 
 constexpr int kTcThreads = 320;     // producer, MMA, 8 epilogue warps
 constexpr int kRows = 128;          // MMA M = TMA box rows = one antenna block
-constexpr int kRowBytes = 128;      // one swizzle span per row
 constexpr uint32_t kTmemCols = 512; // two accumulator sets of 256 columns
 constexpr int kStatusTimeout = 2;
 constexpr int kVB = 2;              // accumulator loads in flight per epilogue thread
@@ -84,6 +86,7 @@ struct TcArgs {
     int stages, KT, W;
     int kt_shift;             // log2(KT): the single-lane roles avoid 64-bit division
     int atoms;                // k-tiles of KT spectra per pipeline stage
+    int row_bytes;            // bytes of one tile row: 64 (FP16 modes) or 128 (FP8)
     int two_tiles;            // stage slots hold separate A and B tiles
     int gs_floats;            // epilogue G buffer (largest 2nb x (2nb + 1) of the modes)
     int slot_rows;            // rows of one operand tile slot in shared memory (<= 128)
@@ -332,6 +335,23 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
+// The same for 64-byte rows: 64-byte swizzle, 8-row groups 512 bytes apart,
+// layout type 4.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(512u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+
+// Operand descriptor of a tile row layout: FP16 modes 64-byte rows, FP8 128.
+template <int MODE>
+__device__ __forceinline__ uint64_t op_desc(uint32_t saddr) {
+    return MODE == 2 ? sw128_desc(saddr) : sw64_desc(saddr);
+}
+
 template <int MODE>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                     uint32_t accumulate) {
@@ -385,7 +405,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
     // operand 2 slot_rows rows) from a slot; rows past the antennas only feed
     // outputs the epilogue ignores, and the ring is followed by enough shared
     // memory for the reads past its last slot.
-    const uint32_t slot = (uint32_t)a.slot_rows * kRowBytes;
+    const uint32_t slot = (uint32_t)a.slot_rows * (uint32_t)a.row_bytes;
+    constexpr int KK = MODE == 2 ? 4 : 2;       // MMA k-steps (32 bytes of a row) per k-tile
     const uint32_t plane_off = slot;                                // hi -> lo plane
     const uint32_t tile_set = planes * slot;                        // operand A -> B
     const uint32_t atom_bytes = tile_set * (a.two_tiles ? 2u : 1u);
@@ -549,21 +570,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                         for (int at = 0; at < n_at; ++at) {
                             const uint32_t ab = base + (uint32_t)at * atom_bytes;
 #pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                const uint64_t ah = sw128_desc(ab + 32u * kk);
+                            for (int kk = 0; kk < KK; ++kk) {
+                                const uint64_t ah = op_desc<MODE>(ab + 32u * kk);
                                 if (MODE == 0) {
-                                    const uint64_t al = sw128_desc(ab + plane_off + 32u * kk);
+                                    const uint64_t al = op_desc<MODE>(ab + plane_off + 32u * kk);
                                     if (diag) {
                                         mma<MODE>(d0, ah, ah, idesc_cat, acc);
                                     } else {
-                                        const uint64_t bh = sw128_desc(ab + tile_set + 32u * kk);
-                                        const uint64_t bl = sw128_desc(ab + tile_set + plane_off + 32u * kk);
+                                        const uint64_t bh = op_desc<MODE>(ab + tile_set + 32u * kk);
+                                        const uint64_t bl = op_desc<MODE>(ab + tile_set + plane_off + 32u * kk);
                                         mma<MODE>(d0, ah, bh, idesc, acc);
                                         mma<MODE>(d0, ah, bl, idesc, 1u);
                                         mma<MODE>(d0, al, bh, idesc, 1u);
                                     }
                                 } else {
-                                    const uint64_t bd = diag ? ah : sw128_desc(ab + tile_set + 32u * kk);
+                                    const uint64_t bd = diag ? ah : op_desc<MODE>(ab + tile_set + 32u * kk);
                                     mma<MODE>(d0, ah, bd, idesc, acc);
                                 }
                                 acc = 1;
@@ -713,8 +734,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                                 li = pl / nb2;
                                 lj = pl - li * nb2;
                             }
-                            const float re = Gs[li * ldg + lj] + Gs[(nb1 + li) * ldg + nb2 + lj];
-                            const float im = Gs[(nb1 + li) * ldg + lj] - Gs[li * ldg + nb2 + lj];
+                            // block rows 2 i' (Re) and 2 i' + 1 (Im)
+                            const float* g0 = Gs + (2 * li) * ldg + 2 * lj;
+                            const float re = g0[0] + g0[ldg + 1];
+                            const float im = g0[ldg] - g0[1];
                             const int i = 64 * itm.b1 + li;
                             const int j = 64 * itm.b2 + lj;
                             float f;
@@ -838,7 +861,8 @@ struct DealPlan {
 
 struct TcPlan {
     int N = 0, C = 0, P = 0, nblk = 1, npairs = 1;
-    int mode = 0, planes = 1, KT = 64;
+    int mode = 0, planes = 1, KT = 32;
+    int row_bytes = 64;       // tile row: 32 FP16 values, or 128 FP8
     int num_sms = 0;
     int box_rows = 128;       // TMA box rows: 2N rounded up to 8 for one block, else 128
     CUtensorMap tmap;
@@ -871,7 +895,8 @@ int tc_plan_create(TcPlan** out, int N, int C, int spec_type, std::string& err) 
     p->npairs = p->nblk * (p->nblk + 1) / 2;
     p->mode = spec_type == SPEC_F16X2 ? 0 : (spec_type == SPEC_F16 ? 1 : 2);
     p->planes = p->mode == 0 ? 2 : 1;
-    p->KT = p->mode == 2 ? 128 : 64;
+    p->KT = p->mode == 2 ? 128 : 32;
+    p->row_bytes = p->mode == 2 ? 128 : 64;
     p->box_rows = p->nblk == 1 ? (2 * N + 7) / 8 * 8 : kRows;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -881,7 +906,7 @@ int tc_plan_create(TcPlan** out, int N, int C, int spec_type, std::string& err) 
         return CORR_ECUDA;
     }
     const size_t tb = (size_t)p->C * p->npairs * sizeof(int);
-    if (cudaMalloc((void**)&p->ticket, tb) != cudaSuccess || cudaMemset(p->ticket, 0, tb) != cudaSuccess) {
+    if (dev_malloc((void**)&p->ticket, tb) != cudaSuccess || cudaMemset(p->ticket, 0, tb) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(p->ticket);
         delete p;
@@ -906,7 +931,7 @@ int tc_plan_update(TcPlan* p, void* spec, int64_t cap, int N, int C, int spec_ty
     const int eb = spec_elem_bytes(spec_type);
     const int R2 = 2 * p->N;
     // tile-major workspace: [plane][cap/T tiles][C][2N rows][T frames], T = KT
-    const int T = kRowBytes / eb;
+    const int T = p->row_bytes / eb;
     cuuint64_t dims[4] = {(cuuint64_t)T, (cuuint64_t)R2, (cuuint64_t)p->C,
                           (cuuint64_t)p->planes * (cap / T)};
     cuuint64_t strides[3] = {(cuuint64_t)T * eb, (cuuint64_t)R2 * T * eb,
@@ -916,7 +941,8 @@ int tc_plan_update(TcPlan* p, void* spec, int64_t cap, int N, int C, int spec_ty
     const CUtensorMapDataType dt =
         eb == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
     CUresult r = get_encoder()(&p->tmap, dt, 4, spec, dims, strides, box, estr,
-                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               p->row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         char buf[128];
@@ -932,8 +958,8 @@ int tc_plan_update(TcPlan* p, void* spec, int64_t cap, int N, int C, int spec_ty
 }
 
 int tc_set_tiles(TcPlan* p, int window, int stages, int split, int atoms, std::string& err) {
-    if (atoms < 0 || atoms > 4) {
-        err = "atoms must be in [0, 4]";
+    if (atoms < 0 || atoms > 8) {
+        err = "atoms must be in [0, 8]";
         return CORR_EINVAL;
     }
     if (split < 0 || split > 64) {
@@ -941,7 +967,7 @@ int tc_set_tiles(TcPlan* p, int window, int stages, int split, int atoms, std::s
         return CORR_EINVAL;
     }
     if (window != 0 && (window < p->KT || window % p->KT || window > 4096)) {
-        err = "window must be a multiple of the k-tile (64 spectra, 128 for FP8) up to 4096";
+        err = "window must be a multiple of the k-tile (32 spectra, 128 for FP8) up to 4096";
         return CORR_EINVAL;
     }
     if (stages != 0 && (stages < 2 || stages > 16)) {
@@ -983,23 +1009,24 @@ LaunchShape launch_shape(TcPlan* const* plans, int n) {
     L.gs_floats = r2max * (r2max + 1);
     L.slot_rows = 8;
     for (int m = 0; m < n; ++m) L.slot_rows = std::max(L.slot_rows, plans[m]->box_rows);
-    const size_t slot = (size_t)L.slot_rows * kRowBytes;
+    const size_t slot = (size_t)L.slot_rows * plans[0]->row_bytes;
     // + the rows an MMA reads past the ring's last slot
     const size_t fixed = 1024 + (size_t)L.gs_floats * 4 + 16 + 16 + 8 * (2 * 16 + 5) + 256 +
-                         (size_t)(kRows - L.slot_rows) * kRowBytes;
+                         (size_t)(kRows - L.slot_rows) * plans[0]->row_bytes;
     auto fit = [&](int atoms) {
         const size_t sb = (size_t)plans[0]->planes * atoms * slot * (L.two_tiles ? 2 : 1);
         return std::min<int>(16, (int)((kSmemBudget - fixed) / sb));
     };
-    // k-tiles per stage, unless set: as many (up to 4) as still leave 3
-    // stages; with two tiles per k-tile (several antenna blocks) 2 stages
-    // suffice -- each stage handshake costs a fixed latency, measured at
-    // N = 256: 2 x 2 k-tiles 1.10 ms against 4 x 1 k-tile 1.24 ms per pass
+    // k-tiles per stage, unless set: as many (up to 256 spectra: 8 k-tiles of
+    // 32, or 4 of the FP8 mode's 128) as still leave 3 stages; with two tiles
+    // per k-tile (several antenna blocks) 2 stages suffice -- each stage
+    // handshake costs a fixed latency, measured at N = 256: 2 stages of 128
+    // spectra 1.10 ms against 4 of 64 1.24 ms per pass
     L.atoms = plans[0]->atoms;
     if (!L.atoms) {
         L.atoms = 1;
         const int min_stages = L.two_tiles ? 2 : 3;
-        for (int at = 4; at > 1; at /= 2)
+        for (int at = plans[0]->KT == 32 ? 8 : 4; at > 1; at /= 2)
             if (fit(at) >= min_stages) {
                 L.atoms = at;
                 break;
@@ -1164,7 +1191,8 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
     a.n_modes = n;
     a.stages = L.stages;
     a.KT = plans[0]->KT;
-    a.kt_shift = a.KT == 128 ? 7 : 6;
+    a.kt_shift = a.KT == 128 ? 7 : 5;
+    a.row_bytes = plans[0]->row_bytes;
     a.W = L.W;
     a.atoms = L.atoms;
     a.two_tiles = L.two_tiles;
@@ -1203,7 +1231,7 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
         d.split = runs[m].split;
         d.tiles = d.S_pad / p->KT;
         d.cap_tiles = (int)(p->cap / p->KT);
-        d.box_bytes = (uint32_t)p->box_rows * kRowBytes;
+        d.box_bytes = (uint32_t)p->box_rows * p->row_bytes;
         d.unit_base = units;
         for (int pr = 0; pr < p->npairs; ++pr)
             units += item_units(d.tiles, host_pair_units(pr, p->nblk)) * p->C;

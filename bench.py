@@ -45,14 +45,15 @@ PROF_EVERY = 10
 # 770e6 B/s of 4-bit samples = 1.54e9 antenna-samples/s (Sec. 1, abstract).
 PAPER_RATE = N_ANT * RATE
 
-# DRAM bytes (read + write) of one full 2048-frame launch of the dominant
-# kernel, from one ncu capture of the current kernels (summaries under
-# profiles/); scaled to the average launch below.  Remove an entry when its
-# kernel changes.
-NCU_TRAFFIC_2048 = {
-    ("fengine", "fp32"): (145.64e6, "ncu --set full, fengine_k512<SPEC_F16X2, corrections off>, "
-                                    "one 2048-frame launch: 23.10 MB read + 122.54 MB written "
-                                    "(profiles/fengine_k512_n44_2048frames_fp32.txt)"),
+# DRAM bytes (read + write) of one launch of the dominant kernel over the
+# given number of frames, from one ncu capture of the current kernels
+# (summaries under profiles/); scaled to the average launch below.  Remove an
+# entry when its kernel changes.
+NCU_TRAFFIC = {
+    ("fengine", "fp32"): (145.64e6, 2048,
+                          "ncu --set full, fengine_k512<SPEC_F16X2, corrections off>, one "
+                          "2048-frame launch: 23.10 MB read + 122.54 MB written "
+                          "(profiles/fengine_k512_n44_2048frames_fp32.txt)"),
 }
 
 # Tensor-pipe activity of the X-engine's one pass over a whole 1 s
@@ -414,9 +415,21 @@ def main():
 
     # roofline of the dominant kernel (largest summed event time)
     spec_total = frames * profiled
-    dom = max(("fengine", "xengine"), key=lambda c: prof[c][1])
+    dom = max(("fengine", "xengine", "fused"), key=lambda c: prof[c][1])
     n_launch, ms = prof[dom]
-    if dom == "xengine":
+    if dom == "fused":
+        # One fused F/X launch per integration, its spectra kept in an
+        # L2-resident ring: only the 4-bit input touches HBM, and the kernel is
+        # bound by instruction issue in its F-engine warps.  Reported here: the
+        # F-engine warps' transform work (the paper's 2.5 K log2 K flops per
+        # spectrum) against the FP32 pipe; the X-engine warps' tensor work is in
+        # the xengine block.
+        work = workload.fengine_flops(N_ANT, K_FFT, spec_total) / n_launch
+        bound, unit = "alu", "TFLOP/s"
+        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+        psrc = f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"
+        achieved = work / (ms / n_launch / 1e3) / 1e12
+    elif dom == "xengine":
         work = workload.xengine_flops(N_ANT, K_FFT, spec_total) / n_launch
         if args.dtype == "fp32_simt":
             bound, unit = "alu", "TFLOP/s"
@@ -438,12 +451,12 @@ def main():
         psrc = f"{peak_src} hbm_gbs"
         achieved = work / (ms / n_launch / 1e3) / 1e9
     traffic = None
-    tr = NCU_TRAFFIC_2048.get((dom, args.dtype))
+    tr = NCU_TRAFFIC.get((dom, args.dtype))
     if tr and not args.chunk:
-        traffic = tr[0] * (spec_total / n_launch) / CHUNK_FRAMES
+        traffic = tr[0] * (spec_total / n_launch) / tr[1]
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": traffic,
-                "traffic_source": tr[1] if traffic else None, "peak_source": psrc,
+                "traffic_source": tr[2] if traffic else None, "peak_source": psrc,
                 "work_per_launch": work,
                 "kernel_ms": {c: prof[c][1] for c in prof},
                 "kernel_launches": {c: prof[c][0] for c in prof},
@@ -454,15 +467,18 @@ def main():
     # three FP16 products of FP32 mode), against the peak of the MMA kind
     # it issues, per CUDA-event time of its launches
     xengine = None
-    if args.dtype != "fp32_simt" and prof["xengine"][0] > 0:
-        n_x, ms_x = prof["xengine"]
+    xkey = "fused" if prof["fused"][0] > 0 else "xengine"
+    if args.dtype != "fp32_simt" and prof[xkey][0] > 0:
+        # (in the fused kernel the X-engine warps run beside the F-engine
+        # warps, so the rates are over the whole fused kernel's time)
+        n_x, ms_x = prof[xkey]
         s_pad = -(-frames // 128) * 128          # every step's passes, padded frames
         sec = ms_x / 1e3
         useful = workload.xengine_flops(N_ANT, K_FFT, frames) * profiled / sec / 1e12
         issued = workload.xengine_issued_flops(N_ANT, K_FFT, s_pad, args.dtype) * profiled / sec / 1e12
         ratio = 2.0 if args.dtype == "fp8" else 1.0
         xengine = {
-            "kernel": "xengine_tc_kernel",
+            "kernel": "fx_fused_kernel (X-engine warps)" if xkey == "fused" else "xengine_tc_kernel",
             "instruction": "tcgen05.mma kind::f8f6f4" if args.dtype == "fp8" else "tcgen05.mma kind::f16",
             "ms_per_step": ms_x / profiled, "launches_per_step": n_x / profiled,
             "useful_tflops": useful, "issued_tflops": issued,
@@ -567,16 +583,19 @@ def main():
 
 def measure_variants(corr, torch, np, dev_in, pushes, rec, main_dtype, chunk, steps=20):
     """Throughput of each X-engine precision and its normalised visibility
-    error against the FP32 tensor-core path on the same 1 s integration."""
+    error against the FP32 tensor-core path on the same 1 s integration;
+    fp32_fused is FP32 mode on the fused F/X-engine (corr_set_fused)."""
     out = {}
     ref = None
-    order = ["fp32", "fp32_simt", "fp16", "fp8"]
+    order = ["fp32", "fp32_fused", "fp32_simt", "fp16", "fp8"]
     res = {}
     for name in order:
         try:
-            h = corr.corr_create(N_ANT, K_FFT, corr.DTYPES[name])
+            h = corr.corr_create(N_ANT, K_FFT, corr.DTYPES[name.replace("_fused", "")])
             if chunk:
                 corr.corr_set_chunk(h, chunk)
+            if name == "fp32_fused":         # the fused F/X-engine (one launch per integration)
+                corr.corr_set_fused(h, True)
         except corr.CorrError as e:
             out[name] = {"unavailable": str(e)}
             continue
@@ -605,7 +624,7 @@ def measure_variants(corr, torch, np, dev_in, pushes, rec, main_dtype, chunk, st
         corr.corr_destroy(h)
         res[name] = V
         val = N_ANT * SPEC_PER_STEP * K_FFT * steps / t
-        out[name] = {"value": val, "rtf": val / (N_ANT * RATE)}
+        out[name] = {"value": val, "rtf": val / (N_ANT * RATE), "ms_per_step": 1e3 * t / steps}
     ref = res.get("fp32")
     if ref is not None:
         autos = [i * N_ANT - i * (i - 1) // 2 for i in range(N_ANT)]

@@ -166,8 +166,28 @@ int corr_set_sample_delays(corr_t h, const int32_t* delays);
 /* Correlate n samples per antenna (n a multiple of K, n >= 0) and add them
  * to the running integration.  `samples` holds n/K frames in the layout
  * above (n*N/2 bytes).  Host memory is staged through the handle's pinned
- * buffers; device memory is read in place. */
+ * buffers; device memory is read in place.  With the fused F/X-engine on
+ * (corr_set_fused) device-memory pushes are recorded and queued as one
+ * launch at the next corr_dump, corr_dump_async, corr_sync or call that
+ * changes what they read (or when 262144 frames wait); their buffers must
+ * stay valid until then, as for every device push. */
 int corr_push(corr_t h, const uint8_t* samples, int64_t n);
+
+/* Fused F/X-engine (no counterpart in the paper's two-core design, Sec. 3):
+ * for K = 512, CORR_FP32 and N <= 44 the transform and the cross-multiply
+ * run as one persistent kernel per run of device-memory pushes, every SM
+ * holding F-engine and X-engine warps, the spectra passed through a ring of
+ * workspace slots that stays in L2 instead of a workspace in HBM.  Off by
+ * default: on a GB300 at N = 44 the separate F- and X-engine launches are
+ * faster (2.46 against 3.8 ms per 1 s integration at 35 MS/s).
+ * corr_set_fused(h, 1) turns it on (allocating its ~69 MB ring on the first
+ * call), CORR_EUNSUPPORTED where it is not served (other K, N or dtype, or a
+ * device without cooperative launches); (h, 0) turns it off.  Pushes from
+ * host memory, corr_grad and handles with sample delays use the separate
+ * launches.  corr_get_fused: *on = 1 when device pushes go to the fused
+ * launch. */
+int corr_set_fused(corr_t h, int on);
+int corr_get_fused(corr_t h, int* on);
 
 /* Finish the integration: write V to `vis` ([P][C] complex64, or complex128
  * when vis_fp64 != 0), store the number of spectra summed in *n_spec (may be
@@ -236,7 +256,10 @@ int corr_load_state(corr_t h, const void* buf);
 /* Test hook for the failure path (no counterpart in the paper).  kind 1: in
  * the next tensor-core X-engine launch, the first work item of CTA 0 never
  * receives its first operand tile, so the MMA thread's bounded wait expires
- * after wait_limit_s seconds (0.001..10).  The kernel then records a status
+ * after wait_limit_s seconds (0.001..10).  kind 2: in the next fused
+ * F/X-engine launch the first chunk never counts as complete, so every
+ * CTA's producer wait expires after wait_limit_s (or stops when another CTA
+ * records its status); the F-engine warps stop at their next task.  The kernel then records a status
  * word, drains its own copies, frees its tensor memory and returns; the
  * next corr_dump / corr_sync reports CORR_ETIMEOUT and the handle stays
  * usable.  No GPU fault, trap or hang is involved. */
@@ -248,7 +271,8 @@ enum corr_kernel {
     CORR_KERNEL_XENGINE = 1, /* cross-multiply-accumulate                  */
     CORR_KERNEL_REDUCE = 2,  /* FP64 accumulation of the X-engine partials */
     CORR_KERNEL_DUMP = 3,    /* accumulator -> [P][C] output               */
-    CORR_KERNEL_COUNT = 4
+    CORR_KERNEL_FUSED = 4,   /* fused F/X-engine (corr_set_fused)          */
+    CORR_KERNEL_COUNT = 5
 };
 
 /* Instrumentation (no counterpart in the paper): while enabled, every kernel

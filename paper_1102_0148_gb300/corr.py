@@ -25,7 +25,7 @@ CORR_FP32, CORR_FP16, CORR_FP8E4M3, CORR_FP32_SIMT = 0, 1, 2, 3
 CORR_OK, CORR_EINVAL, CORR_ENOMEM, CORR_ECUDA, CORR_ETIMEOUT, CORR_ESTATE, CORR_EUNSUPPORTED = (
     0, -1, -2, -3, -4, -5, -6)
 CORR_MAX_N = 512
-KERNEL_CLASSES = ("fengine", "xengine", "reduce", "dump")
+KERNEL_CLASSES = ("fengine", "xengine", "reduce", "dump", "fused")
 
 DTYPES = {"fp32": CORR_FP32, "fp16": CORR_FP16, "fp8": CORR_FP8E4M3, "fp32_simt": CORR_FP32_SIMT}
 
@@ -38,6 +38,8 @@ _SIGS = {
     "corr_set_stream": (_int, [_vp, _vp]),
     "corr_set_chunk": (_int, [_vp, _i64]),
     "corr_set_tiles": (_int, [_vp, _int, _int, _int, _int]),
+    "corr_set_fused": (_int, [_vp, _int]),
+    "corr_get_fused": (_int, [_vp, ctypes.POINTER(_int)]),
     "corr_test_fault": (_int, [_vp, _int, ctypes.c_double]),
     "corr_state_bytes": (_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "corr_save_state": (_int, [_vp, _vp]),
@@ -146,6 +148,16 @@ def corr_save_state(h):
 def corr_load_state(h, state):
     buf = ctypes.create_string_buffer(state, len(state))
     return _check(_lib.corr_load_state(h, buf), h)
+
+
+def corr_set_fused(h, on=True):
+    return _check(_lib.corr_set_fused(h, 1 if on else 0), h)
+
+
+def corr_get_fused(h):
+    v = _int()
+    _check(_lib.corr_get_fused(h, ctypes.byref(v)), h)
+    return bool(v.value)
 
 
 def corr_test_fault(h, kind, wait_limit_s):
@@ -328,7 +340,9 @@ def corr_batch_last_error(b):
 class Correlator:
     """Owning wrapper: ``with Correlator(44, 512) as c: c.push(x); V, n = c.dump()``."""
 
-    def __init__(self, N, K, dtype=CORR_FP32, chunk=None, stream=None):
+    def __init__(self, N, K, dtype=CORR_FP32, chunk=None, stream=None, fused=None):
+        if isinstance(dtype, str):
+            dtype = DTYPES[dtype]
         self.h = corr_create(N, K, dtype)
         info = corr_info(self.h)
         self.N, self.K, self.C, self.P, self.dtype = (info[k] for k in ("N", "K", "C", "P", "dtype"))
@@ -336,6 +350,8 @@ class Correlator:
             corr_set_chunk(self.h, chunk)
         if stream is not None:
             corr_set_stream(self.h, stream)
+        if fused is not None:
+            corr_set_fused(self.h, fused)
 
     def set_corrections(self, gains=None, delays=None):
         corr_set_corrections(self.h, gains, delays)

@@ -2,6 +2,7 @@
 // plan, the push loop that drives F-engine -> X-engine -> FP64 reduction per
 // workspace pass, and the dump.
 #include "corr_internal.h"
+#include "fx_fused.h"
 #include "xengine_tc.h"
 
 #include <cmath>
@@ -103,12 +104,18 @@ struct corr_s {
     int64_t fill = 0;            // frames waiting in the workspace for the X-engine
     double2* fill_acc = nullptr; // accumulator those frames belong to
     TcPlan* tc = nullptr;
+    // fused F/X-engine (K = 512, FP32 mode, N <= 48): device-input pushes
+    // wait here and run as one persistent launch at the next flush
+    FxPlan* fx = nullptr;
+    bool fx_on = false;
+    std::vector<FxSegment> fx_pending;
+    int64_t fx_pending_blocks = 0;
     // instrumentation: CUDA event pairs per kernel class
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[CORR_KERNEL_COUNT];
-    int64_t prof_launches[CORR_KERNEL_COUNT] = {0, 0, 0, 0};
-    double prof_ms[CORR_KERNEL_COUNT] = {0, 0, 0, 0};
+    int64_t prof_launches[CORR_KERNEL_COUNT] = {};
+    double prof_ms[CORR_KERNEL_COUNT] = {};
     cudaEvent_t ev_open = nullptr;
     std::string err = "no error";
 };
@@ -395,8 +402,48 @@ int xengine_pass(corr_t h, int64_t S_pad, double2* acc) {
     return CORR_OK;
 }
 
-// X-engine over the frames waiting in the workspace.
+// The fused launch over the device-input pushes waiting for it.
+int fx_flush(corr_t h) {
+    if (h->fx_pending.empty()) return CORR_OK;
+    prof_begin(h);
+    int rc = fx_launch(h->fx, h->fx_pending.data(), (int)h->fx_pending.size(), h->twiddle,
+                       split_table(h, false), h->corr_on ? h->corr_tab : nullptr, h->acc, h->status,
+                       h->stream, h->err);
+    h->fx_pending.clear();
+    h->fx_pending_blocks = 0;
+    if (rc != CORR_OK) return rc;
+    prof_end(h, CORR_KERNEL_FUSED);
+    return CORR_OK;
+}
+
+// Whether device-input pushes of this handle go to the fused launch.
+bool fx_usable(corr_t h) { return h->fx && h->fx_on && !h->sdelay_on; }
+
+// Record S frames of device input for the next fused launch (launching the
+// waiting ones first when the block table would overflow).
+int fx_append(corr_t h, const uint8_t* din, int64_t S) {
+    const int64_t rec = (int64_t)h->N * (h->K / 2);
+    while (S > 0) {
+        const int64_t room = (int64_t)kFxMaxBlocks - h->fx_pending_blocks;
+        if (room <= 0) {
+            int rc = fx_flush(h);
+            if (rc != CORR_OK) return rc;
+            continue;
+        }
+        const int64_t take = std::min<int64_t>(S, room * 32);
+        h->fx_pending.push_back(FxSegment{din, take});
+        h->fx_pending_blocks += (take + 31) / 32;
+        din += take * rec;
+        S -= take;
+    }
+    return CORR_OK;
+}
+
+// X-engine over the frames waiting in the workspace (and the fused launch
+// over the pushes waiting for it).
 int flush(corr_t h) {
+    int frc = fx_flush(h);
+    if (frc != CORR_OK) return frc;
     int jrc = join_fengines(h);
     if (jrc != CORR_OK) return jrc;
     if (h->fill == 0) return CORR_OK;
@@ -469,6 +516,10 @@ int process_samples(corr_t h, const uint8_t* samples, int64_t n, bool raw, doubl
     const int64_t frames = n / h->K;
     const int64_t rec = (int64_t)h->N * (h->K / 2);
     const bool host = !is_device_ptr(samples);
+    // (the fused F-engine reads 16 bytes per lane: 16-byte aligned input only)
+    if (!host && !raw && acc == h->acc && fx_usable(h) &&
+        (reinterpret_cast<uintptr_t>(samples) & 15) == 0)
+        return fx_append(h, samples, frames);
     if (host && !h->stage[0]) {
         // ~32 MB per buffer (whole 128-frame blocks), 16 of them: the copies
         // (~205 GB/s from pinned host memory) can run ~2.5 ms ahead of the
@@ -565,6 +616,7 @@ void destroy_impl(corr_t h) {
     }
     free_stages(h);
     if (h->tc) tc_plan_destroy(h->tc);
+    if (h->fx) fx_plan_destroy(h->fx);
     for (auto& v : h->ev_pending)
         for (auto& pr : v) {
             cudaEventDestroy(pr.first);
@@ -660,6 +712,7 @@ int corr_create(corr_t* out, int N, int K, int dtype) {
         int rc = tc_plan_create(&h->tc, N, h->C, h->spec_type, h->err);
         if (rc != CORR_OK) return bail(rc);
     }
+    // the fused F/X-engine is off until corr_set_fused(h, 1) makes its plan
 
     // Twiddles W_K^m = exp(-2 pi i m / K), from an exact integer angle in FP64.
     std::vector<float2> tw(K);
@@ -724,6 +777,8 @@ int corr_create(corr_t* out, int N, int K, int dtype) {
 
 int corr_set_stream(corr_t h, void* stream) {
     if (!h) return CORR_EINVAL;
+    int frc = fx_flush(h);
+    if (frc != CORR_OK) return frc;
     int jrc = join_fengines(h);
     if (jrc != CORR_OK) return jrc;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -746,6 +801,28 @@ int corr_set_chunk(corr_t h, int64_t max_spectra) {
     if (jrc != CORR_OK) return jrc;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return alloc_workspace(h, max_spectra);
+}
+
+int corr_set_fused(corr_t h, int on) {
+    if (!h) return CORR_EINVAL;
+    if (on && !h->fx) {
+        if (!fx_supported(h->N, h->K, h->spec_type))
+            return set_err(h, CORR_EUNSUPPORTED,
+                           "the fused F/X-engine serves K = 512, CORR_FP32, N <= %d", kFxMaxN);
+        std::string ferr;
+        const int rc = fx_plan_create(&h->fx, h->N, ferr);
+        if (rc != CORR_OK) return set_err(h, rc, "%s", ferr.c_str());
+    }
+    int frc = fx_flush(h);
+    if (frc != CORR_OK) return frc;
+    h->fx_on = on != 0;
+    return CORR_OK;
+}
+
+int corr_get_fused(corr_t h, int* on) {
+    if (!h || !on) return CORR_EINVAL;
+    *on = h->fx && h->fx_on ? 1 : 0;
+    return CORR_OK;
 }
 
 int corr_set_tiles(corr_t h, int window, int stages, int split, int atoms) {
@@ -885,6 +962,14 @@ int corr_load_state(corr_t h, const void* buf) {
 
 int corr_test_fault(corr_t h, int kind, double wait_limit_s) {
     if (!h) return CORR_EINVAL;
+    if (kind == 2) {
+        if (!h->fx || !h->fx_on)
+            return set_err(h, CORR_EINVAL, "the fused-launch fault needs the fused F/X-engine on");
+        int frc = flush(h);
+        if (frc != CORR_OK) return frc;
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        return fx_test_withhold(h->fx, wait_limit_s, h->err);
+    }
     if (kind != 1) return set_err(h, CORR_EINVAL, "unknown fault kind %d", kind);
     if (!h->use_tc) return set_err(h, CORR_EINVAL, "the withheld-copy fault needs a tensor-core handle");
     int jrc = sync_fengines(h);
@@ -934,7 +1019,10 @@ int corr_set_corrections(corr_t h, const float* gains, const float* delays) {
             if (!std::isfinite(th[i]))
                 return set_err(h, CORR_EINVAL, "delay %d is not finite", i);
     }
-    // launches already queued keep the old tables
+    // launches already queued keep the old tables; pushes waiting for the
+    // fused launch are run with them now
+    int frc0 = fx_flush(h);
+    if (frc0 != CORR_OK) return frc0;
     int jrc = join_fengines(h);
     if (jrc != CORR_OK) return jrc;
     // Frames already pushed keep the old corrections and pre-scales: with new

@@ -32,7 +32,10 @@ def test_bounded_wait_timeout_is_reported_and_recovered(lib, dtype):
     packed, _ = synth.make_samples(N, S * K, K, seed=77)
     R, _ = oracle.correlate(packed, N, K)
     dev = torch.from_numpy(packed.reshape(-1)).cuda()
-    with lib.Correlator(N, K, dtype) as c:
+    # kind 1 withholds a copy of the separate tensor-core X-engine, so this
+    # handle keeps the separate F- and X-engine launches (the fused launch's
+    # own hook is tested in test_gpu_fused.py)
+    with lib.Correlator(N, K, dtype, fused=False) as c:
         lib.corr_test_fault(c.h, 1, 0.05)
         c.push(dev, S * K)                       # queued; the X-engine gives up
         with pytest.raises(lib.CorrError) as ei:

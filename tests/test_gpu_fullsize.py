@@ -24,7 +24,7 @@ N, K, RATE = 44, 512, 35e6
 FRAMES = int(RATE // K)                   # 68359
 CHUNK = (1 << 20) // K                    # 2048 frames per push
 CHANNELS = [0, 1, 97, 170, 255]
-BOUND = {"fp32": 1e-5, "fp32_simt": 1e-5, "fp16": 1.2e-5, "fp8": 4e-3}
+BOUND = {"fp32": 1e-5, "fp32_fused": 1e-5, "fp32_simt": 1e-5, "fp16": 1.2e-5, "fp8": 4e-3}
 
 
 @pytest.fixture(scope="module")
@@ -39,11 +39,14 @@ def workload():
     return dev, R
 
 
-@pytest.mark.parametrize("dtype", ["fp32", "fp32_simt", "fp16", "fp8"])
+@pytest.mark.parametrize("dtype", ["fp32", "fp32_fused", "fp32_simt", "fp16", "fp8"])
 def test_one_second_integration(lib, workload, dtype):
+    """fp32: the separate F- and X-engine launches (the default);
+    fp32_fused: the fused F/X-engine."""
     dev, R = workload
     rec = N * K // 2
-    with lib.Correlator(N, K, dtype) as c:
+    fused = True if dtype == "fp32_fused" else None
+    with lib.Correlator(N, K, dtype.replace("_fused", ""), fused=fused) as c:
         for f0 in range(0, FRAMES, CHUNK):
             nf = min(CHUNK, FRAMES - f0)
             lib.corr_push(c.h, dev.data_ptr() + f0 * rec, nf * K)

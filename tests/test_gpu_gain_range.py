@@ -45,7 +45,7 @@ def extreme_gains(seed):
     return g, tau
 
 
-@pytest.mark.parametrize("dtype", ["fp32", "fp32_simt", "fp16"])
+@pytest.mark.parametrize("dtype", ["fp32", "fp32_fused", "fp32_simt", "fp16"])
 @pytest.mark.parametrize("K,S", [(512, 300), (4096, 40)])
 def test_extreme_gains_with_tone(lib, torch_cuda, dtype, K, S):
     N = MODULI.size
@@ -59,7 +59,7 @@ def test_extreme_gains_with_tone(lib, torch_cuda, dtype, K, S):
     assert e <= (FP16_BOUND[K] if dtype == "fp16" else TOL), e
 
 
-@pytest.mark.parametrize("dtype", ["fp32", "fp32_simt"])
+@pytest.mark.parametrize("dtype", ["fp32", "fp32_fused", "fp32_simt"])
 @pytest.mark.parametrize("K", [512, 4096])
 def test_worst_case_input_largest_gain(lib, torch_cuda, dtype, K):
     """Every sample -8 (byte 0x88): |X[0]| = 8K, the bound the pre-scale is

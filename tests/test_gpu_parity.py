@@ -44,7 +44,9 @@ def vis_error(V, R, N):
 
 def run_gpu(lib, torch, packed, N, K, dtype, pushes=None, chunk=None, gains=None, delays=None,
             host=False, fp64=True):
-    c = lib.Correlator(N, K, dtype, chunk=chunk)
+    # "fp32_fused": FP32 mode with the fused F/X-engine on where it is served
+    # (K = 512, N <= 44), the separate launches elsewhere
+    c = fp32_handle(lib, N, K, dtype, chunk=chunk)
     try:
         if gains is not None or delays is not None:
             g = None if gains is None else np.ascontiguousarray(np.asarray(gains, np.complex64))
@@ -69,7 +71,20 @@ def run_gpu(lib, torch, packed, N, K, dtype, pushes=None, chunk=None, gains=None
         c.close()
 
 
-DTYPES_FP32 = ["fp32_simt", "fp32"]
+DTYPES_FP32 = ["fp32_simt", "fp32", "fp32_fused"]
+
+
+def fp32_handle(lib, N, K, dtype, **kw):
+    """A Correlator of `dtype`; "fp32_fused" turns the fused F/X-engine on
+    where it is served."""
+    fused = dtype == "fp32_fused"
+    c = lib.Correlator(N, K, "fp32" if fused else dtype, **kw)
+    if fused:
+        try:
+            lib.corr_set_fused(c.h, True)
+        except lib.CorrError as e:
+            assert e.code == lib.CORR_EUNSUPPORTED
+    return c
 
 
 @pytest.mark.parametrize("N,K,S", [(3, 16, 37), (5, 64, 130), (44, 512, 64), (7, 1024, 9),
@@ -163,7 +178,7 @@ def test_unaligned_input_pointer(lib, torch_cuda, dtype):
     raw[3:3 + packed.size] = torch.from_numpy(packed.reshape(-1)).cuda()
     view = raw[3:3 + packed.size]
     assert view.data_ptr() % 16 == 3
-    with lib.Correlator(N, K, dtype) as c:
+    with fp32_handle(lib, N, K, dtype) as c:
         c.push(view, S * K)
         V, n = c.dump(fp64=True)
     assert n == S and vis_error(V, R, N) <= TOL
@@ -254,7 +269,7 @@ def test_tile_choices_keep_parity(lib, torch_cuda, window, stages, split):
     N, K, S = 44, 512, 600
     packed, _ = synth.make_samples(N, S * K, K, seed=SEED + 21)
     R, _ = oracle.correlate(packed, N, K)
-    with lib.Correlator(N, K, "fp32") as c:
+    with lib.Correlator(N, K, "fp32", fused=False) as c:    # the separate X-engine's tiles
         lib.corr_set_tiles(c.h, window, stages, split)
         c.push(torch_cuda.from_numpy(packed.reshape(-1)).cuda(), S * K)
         V, n = c.dump(fp64=True)

@@ -30,7 +30,7 @@ constexpr int64_t kMaxTcChunk = 131072;
 constexpr int64_t kMinDefaultChunk = 2048;
 constexpr size_t kDefaultWorkspaceBytes = (size_t)2 << 30;
 constexpr size_t kTcWorkspaceBytes = (size_t)8 << 30;
-constexpr int64_t kSimtSplit = 256;   // frames per SIMT X-engine split
+constexpr int64_t kSimtSplit = 256;   // fewest frames per SIMT X-engine split (sizes the partials)
 constexpr int kHostStages = 16;        // device staging buffers for host input
 constexpr size_t kStageBytes = (size_t)32 << 20;   // ~32 MB each
 
@@ -104,7 +104,7 @@ struct corr_s {
     int64_t fill = 0;            // frames waiting in the workspace for the X-engine
     double2* fill_acc = nullptr; // accumulator those frames belong to
     TcPlan* tc = nullptr;
-    // fused F/X-engine (K = 512, FP32 mode, N <= 48): device-input pushes
+    // fused F/X-engine (K = 512, FP32 mode, N <= 44): device-input pushes
     // wait here and run as one persistent launch at the next flush
     FxPlan* fx = nullptr;
     bool fx_on = false;
@@ -172,7 +172,8 @@ int alloc_workspace(corr_t h, int64_t cap) {
     cap = (cap + kSpecPad - 1) / kSpecPad * kSpecPad;
     const size_t eb = (size_t)spec_elem_bytes(h->spec_type);
     const size_t spec_bytes = (size_t)spec_planes(h->spec_type) * h->C * 2 * h->N * cap * eb;
-    // FP32 partials: one per 256-frame split for the CUDA-core X-engine, at
+    // FP32 partials: one per split of at least 256 frames for the CUDA-core
+    // X-engine (its launch picks the split count up to this), at
     // most 8 slots for the tensor cores (their planner's limit)
     int max_split = (int)((cap + kSimtSplit - 1) / kSimtSplit);
     if (h->use_tc) max_split = std::min(max_split, 8);
@@ -386,8 +387,7 @@ int xengine_pass(corr_t h, int64_t S_pad, double2* acc) {
         xa.C = h->C;
         xa.S_pad = S_pad;
         xa.spec_type = h->spec_type;
-        xa.s_per_split = kSimtSplit;
-        xa.n_split = (int)((S_pad + kSimtSplit - 1) / kSimtSplit);
+        xa.max_split = h->max_split;
         xa.partial = h->partial;
         xa.scale = nullptr;
         xa.status = h->status;

@@ -122,14 +122,16 @@ struct XengineArgs {
     int N, C;
     int64_t S_pad;           // frames present (multiple of kSpecPad)
     int spec_type;
-    int64_t s_per_split;     // frames per split (multiple of 128)
-    int n_split;
+    int max_split;           // partial slots available ([max_split][C][P])
+    int64_t s_per_split;     // set by the launch: frames per split (multiple of 32)
+    int n_split;             // set by the launch: splits (<= max_split)
     float2* partial;         // [n_split][C][P]
     const float* scale;      // [N][C] pre-cast scales (FP16/FP8), else nullptr
     int* status;             // device status word (bounded waits)
 };
 
-cudaError_t launch_xengine_simt(const XengineArgs& a, cudaStream_t st);
+// Chooses the split of the pass (a.s_per_split, a.n_split) and launches.
+cudaError_t launch_xengine_simt(XengineArgs& a, cudaStream_t st);
 
 // acc[k][p] += sum over splits of partial[split][k][p], in a fixed order (FP64).
 cudaError_t launch_reduce_partials(const float2* partial, int n_split, int64_t CP,

@@ -55,7 +55,7 @@ CtxGetCurrentFn ctx_get_current() {
     return fn;
 }
 
-constexpr int64_t kSplit = 256;     // frames per X-engine split, as the SIMT handle path
+constexpr int64_t kSplit = 256;     // fewest frames per X-engine split (sizes the partials)
 constexpr int64_t kMaxPass = 2048;  // frames per pass at most
 
 size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -180,8 +180,7 @@ extern "C" int corr_correlate_noalloc(const uint8_t* samples, int64_t n, int N, 
         xa.C = C;
         xa.S_pad = S_pad;
         xa.spec_type = SPEC_F32;
-        xa.s_per_split = kSplit;
-        xa.n_split = (int)((S_pad + kSplit - 1) / kSplit);
+        xa.max_split = max_split;
         xa.partial = part;
         if ((e = launch_xengine_simt(xa, st)) != cudaSuccess) return fail_cuda(e, "X-engine");
         if ((e = launch_reduce_partials(part, xa.n_split, (int64_t)C * P, acc, st)) != cudaSuccess)

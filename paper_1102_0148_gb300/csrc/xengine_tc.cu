@@ -63,10 +63,12 @@ constexpr int kTcThreads = 320;     // producer, MMA, 8 epilogue warps
 constexpr int kRows = 128;          // MMA M = TMA box rows = one antenna block
 constexpr uint32_t kTmemCols = 512; // two accumulator sets of 256 columns
 constexpr int kVB = 2;              // accumulator loads in flight per epilogue thread
+constexpr int kVCols = 16;          // baselines per antenna in one staging round
+constexpr int kVRow = kVCols + 1;   // float2 per staging row (+1: bank offset)
 
 struct TcModeArgs {
     int N, C, P;
-    int nblk, npairs;         // antenna blocks of 64 and their pairs b1 <= b2
+    int nblk, npairs;         // antenna blocks of 64 and the work groups of a channel
     int n_split;
     int item_base, n_items;   // items: block pair fastest, then channel, then split
     int64_t S_pad, S_item;
@@ -89,7 +91,7 @@ struct TcArgs {
     int kt_shift;             // log2(KT): the single-lane roles avoid 64-bit division
     int atoms;                // k-tiles of KT spectra per pipeline stage
     int row_bytes;            // bytes of one tile row: 64 (FP16 modes) or 128 (FP8)
-    int two_tiles;            // stage slots hold separate A and B tiles
+    int wide;                 // a mode has several antenna blocks: atoms hold A, B0, B1 slots
     int gs_floats;            // epilogue G buffer (largest 2nb x (2nb + 1) of the modes)
     int slot_rows;            // rows of one operand tile slot in shared memory (<= 128)
     int* status;
@@ -100,7 +102,7 @@ struct TcArgs {
 };
 
 struct Item {
-    int m, k, b1, b2, sp, pr;
+    int m, k, b1, b2, nbB, sp, pr;
 };
 
 // One CTA's share of an item: k-tiles [s_beg, s_end) of the pass, the
@@ -111,22 +113,44 @@ struct Piece {
     int slot, nslots;
 };
 
-// Work units per k-tile: 2 for a diagonal block pair (one tile loaded, two
-// MMAs in FP32 mode), 3 for an off-diagonal one (two tiles, three MMAs).
-// Each item (with k-tiles) starts with kEndUnits more, standing for the cost
-// of an item's end (~4 k-tiles); they hold no k-tile.
+// Work groups of a channel.  One antenna block (N <= 64): the single
+// diagonal block pair.  Several blocks: block b1 against the blocks
+// b2 .. b2 + nbB - 1 (b2 = b1, b1 + 2, ...; nbB = 2, or 1 for the last one of
+// a row), so one A tile feeds an MMA of N = 256 and a channel's 4 blocks
+// (N = 256 antennas) take 6 groups instead of 10 pairs.
+__host__ __device__ __forceinline__ int groups_of(int nblk) {
+    if (nblk == 1) return 1;
+    int g = 0;
+    for (int b1 = 0; b1 < nblk; ++b1) g += (nblk - b1 + 1) >> 1;
+    return g;
+}
+
+__host__ __device__ __forceinline__ void group_decode(int gi, int nblk, int& b1, int& b2, int& nbB) {
+    b1 = 0;
+    if (nblk > 1)
+        while (gi >= ((nblk - b1 + 1) >> 1)) {
+            gi -= (nblk - b1 + 1) >> 1;
+            ++b1;
+        }
+    b2 = b1 + 2 * gi;
+    nbB = nblk == 1 ? 1 : (nblk - b2 < 2 ? nblk - b2 : 2);
+}
+
+// Work units per k-tile: 2 for the single diagonal pair (one tile loaded,
+// two MMAs in FP32 mode); for a group, one per tile loaded (an A tile that
+// is the group's first B block is not loaded again) plus one.  Each item
+// (with k-tiles) starts with kEndUnits more, standing for the cost of an
+// item's end (~4 k-tiles); they hold no k-tile.
 constexpr int kEndUnits = 8;
 
 __host__ __device__ __forceinline__ int64_t item_units(int64_t tiles, int w) {
     return tiles > 0 ? kEndUnits + tiles * w : 0;
 }
-__device__ __forceinline__ int pair_units(int pr, int nblk) {
-    int b1 = 0;
-    while (pr >= nblk - b1) {
-        pr -= nblk - b1;
-        ++b1;
-    }
-    return pr == 0 ? 2 : 3;
+__host__ __device__ __forceinline__ int pair_units(int gi, int nblk) {
+    if (nblk == 1) return 2;
+    int b1, b2, nbB;
+    group_decode(gi, nblk, b1, b2, nbB);
+    return nbB + (b2 != b1 ? 1 : 0) + 1;
 }
 
 __device__ __forceinline__ Item decode_item(const TcArgs& a, int g) {
@@ -136,20 +160,14 @@ __device__ __forceinline__ Item decode_item(const TcArgs& a, int g) {
     int l = g - d.item_base;
     Item it;
     it.m = m;
-    // block pair fastest: the CTAs that take one channel's pairs at the same
+    // group fastest: the CTAs that take one channel's groups at the same
     // time share its block tiles through L2
-    int pr = l % d.npairs;
+    const int pr = l % d.npairs;
     l /= d.npairs;
     it.pr = pr;
     it.k = l % d.C;
     it.sp = l / d.C;
-    int b1 = 0;
-    while (pr >= d.nblk - b1) {
-        pr -= d.nblk - b1;
-        ++b1;
-    }
-    it.b1 = b1;
-    it.b2 = b1 + pr;
+    group_decode(pr, d.nblk, it.b1, it.b2, it.nbB);
     return it;
 }
 
@@ -217,16 +235,10 @@ __device__ __forceinline__ bool next_piece(const TcArgs& a, PieceCursor& c, Piec
         const int64_t j1 = c.hi > t0 ? min(d.tiles, ceil_div64(c.hi - t0, w)) : 0;
         const bool mine = j0 < j1;
         if (mine) {
-            int pr = c.pr, b1 = 0;
-            while (pr >= d.nblk - b1) {
-                pr -= d.nblk - b1;
-                ++b1;
-            }
             p.itm.m = c.m;
             p.itm.k = c.k;
             p.itm.pr = c.pr;
-            p.itm.b1 = b1;
-            p.itm.b2 = b1 + pr;
+            group_decode(c.pr, d.nblk, p.itm.b1, p.itm.b2, p.itm.nbB);
             p.itm.sp = 0;
             const int64_t KT = a.KT;
             p.s_beg = j0 * KT;
@@ -260,30 +272,38 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" :::
 
 // --------------------------------------------------------------------- kernel
 
-template <int MODE>
+// WIDE: some mode of the launch has several antenna blocks (work groups of
+// one A block and two B blocks); launches of single-block modes only take
+// the narrow instance, which has none of the group code.
+template <int MODE, bool WIDE>
 __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_constant__ TcArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     constexpr int planes = MODE == 0 ? 2 : 1;
-    // stage layout: [operand A|B][plane][atom] tiles of 16 KB
-    // Stage layout: per k-tile ("atom") [operand A | operand B][plane hi | lo],
-    // each a slot of slot_rows rows (2N rounded up to 8 for one antenna block,
-    // else 128).  The MMA reads 128 rows (and a diagonal pair's concatenated B
-    // operand 2 slot_rows rows) from a slot; rows past the antennas only feed
-    // outputs the epilogue ignores, and the ring is followed by enough shared
-    // memory for the reads past its last slot.
+    // Stage layout: per k-tile ("atom") the A slot of each plane [hi | lo];
+    // when a mode of the launch has several antenna blocks (WIDE), then the
+    // B slots [B0 hi | B1 hi | B0 lo | B1 lo] (one plane: [B0 | B1]), so a
+    // group's two B blocks form one operand of 256 rows.  A slot has
+    // slot_rows rows (2N rounded up to 8 for one antenna block, else 128).
+    // The MMA reads 128 rows (and a single-block pair's concatenated B operand
+    // 2 slot_rows rows) from a slot; rows past the antennas only feed outputs
+    // the epilogue ignores, and the ring is followed by enough shared memory
+    // for the reads past its last slot.
     const uint32_t slot = (uint32_t)a.slot_rows * (uint32_t)a.row_bytes;
     constexpr int KK = MODE == 2 ? 4 : 2;       // MMA k-steps (32 bytes of a row) per k-tile
-    const uint32_t plane_off = slot;                                // hi -> lo plane
-    const uint32_t tile_set = planes * slot;                        // operand A -> B
-    const uint32_t atom_bytes = tile_set * (a.two_tiles ? 2u : 1u);
+    const uint32_t plane_off = slot;                                // A: hi -> lo plane
+    const uint32_t bh_off = planes * slot;                          // B0 hi (B1 hi follows)
+    const uint32_t bl_off = bh_off + 2 * slot;                      // B0 lo (planes == 2)
+    const uint32_t atom_bytes = planes * slot * (WIDE ? 3u : 1u);
     const uint32_t stage_bytes = atom_bytes * (uint32_t)a.atoms;
     const int step = a.KT * a.atoms;                             // spectra per stage
     unsigned char* stages = smem;
     float* Gs = reinterpret_cast<float*>(smem + a.stages * stage_bytes);   // <= 128 x 129
+    // WIDE: each epilogue warp's staging rows for V, [16][kVRow] float2
+    float2* vstage = reinterpret_cast<float2*>(Gs + a.gs_floats);
     uint64_t* bars = reinterpret_cast<uint64_t*>(
-        (reinterpret_cast<uintptr_t>(Gs + a.gs_floats) + 15) & ~(uintptr_t)15);
+        (reinterpret_cast<uintptr_t>(vstage + (WIDE ? 8 * 16 * kVRow : 0)) + 15) & ~(uintptr_t)15);
     uint64_t* full = bars;
     uint64_t* empty = full + a.stages;
     uint64_t* accf = empty + a.stages;
@@ -296,6 +316,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
         (reinterpret_cast<uintptr_t>(epi_last + 2) + 15) & ~(uintptr_t)15);
     Piece* epi_pc = reinterpret_cast<Piece*>(epi_cur + 1);
     volatile int* epi_more = reinterpret_cast<volatile int*>(epi_pc + 1);
+    volatile int* epi_abort = epi_more + 1;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -339,9 +360,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                 const Item& itm = pc.itm;
                 const TcModeArgs& d = a.md[itm.m];
                 const CUtensorMap* map = &a.tmap[itm.m];
-                const bool diag = itm.b1 == itm.b2;
+                const bool single = !WIDE || d.nblk == 1;  // one block: A = B, one tile
+                const bool alias = !single && itm.b2 == itm.b1;   // A is the group's first B block
                 const int ra = kRows * itm.b1;
                 const int rb = kRows * itm.b2;
+                const uint32_t ntile = single ? 1u : (uint32_t)itm.nbB + (alias ? 0u : 1u);
                 const int64_t s_beg = pc.s_beg;
                 const int64_t s_end = pc.s_end;
                 for (int64_t s = s_beg; s < s_end; s += step, ++it) {
@@ -355,23 +378,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                     }
                     if (a.withhold && blockIdx.x == 0 && it == 0) continue;   // test hook
                     const int n_at = (int)min((int64_t)a.atoms, (s_end - s) >> a.kt_shift);
-                    const uint32_t bytes =
-                        (uint32_t)n_at * planes * d.box_bytes * (diag ? 1u : 2u);
+                    const uint32_t bytes = (uint32_t)n_at * planes * d.box_bytes * ntile;
                     const uint32_t fb = smem_u32(&full[st]);
                     mbar_expect_tx(fb, bytes);
                     const uint32_t dst = smem_u32(stages + st * stage_bytes);
                     for (int at = 0; at < n_at; ++at) {
                         const int st4 = (int)(s >> a.kt_shift) + at;   // k-tile of the pass
                         const uint32_t o = (uint32_t)at * atom_bytes;
-                        tma_load_4d(dst + o, map, fb, ra, itm.k, st4);
-                        if (planes == 2)
-                            tma_load_4d(dst + plane_off + o, map, fb, ra, itm.k, d.cap_tiles + st4);
-                        if (!diag) {
-                            tma_load_4d(dst + tile_set + o, map, fb, rb, itm.k, st4);
+                        if (!alias) {
+                            tma_load_4d(dst + o, map, fb, ra, itm.k, st4);
                             if (planes == 2)
-                                tma_load_4d(dst + tile_set + plane_off + o, map, fb, rb, itm.k,
-                                            d.cap_tiles + st4);
+                                tma_load_4d(dst + plane_off + o, map, fb, ra, itm.k, d.cap_tiles + st4);
                         }
+                        if (!single)
+                            for (int bb = 0; bb < itm.nbB; ++bb) {
+                                tma_load_4d(dst + bh_off + bb * slot + o, map, fb, rb + kRows * bb,
+                                            itm.k, st4);
+                                if (planes == 2)
+                                    tma_load_4d(dst + bl_off + bb * slot + o, map, fb, rb + kRows * bb,
+                                                itm.k, d.cap_tiles + st4);
+                            }
                     }
                     armed |= 1u << st;
                     armed_ph = (armed_ph & ~(1u << st)) | (ph << st);
@@ -400,12 +426,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
             while (ok && next_piece(a, cur, pc)) {
                 const Item& itm = pc.itm;
                 const TcModeArgs& d = a.md[itm.m];
-                const bool diag = itm.b1 == itm.b2;
-                const int Nn = (2 * block_ants(d.N, itm.b2) + 15) & ~15;
+                const bool single = !WIDE || d.nblk == 1;
+                const bool alias = !single && itm.b2 == itm.b1;
+                // single block: N = 2N rounded up to 16; group: N = 128 per B block
+                const int Nn = single ? (2 * block_ants(d.N, 0) + 15) & ~15 : kRows * itm.nbB;
                 // D = F32, A/B = F16 (kind::f16) or E4M3 (kind::f8f6f4), K-major,
                 // N>>3 at bits 17-22, M>>4 at bits 24-28
                 const uint32_t idesc =
                     (1u << 4) | ((uint32_t)(Nn >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+                // group: A from its own slots, or the first B block's
+                const uint32_t a_hi = alias ? bh_off : 0u;
+                const uint32_t a_lo = alias ? bl_off : plane_off;
                 // FP32 mode, diagonal pair: B = [hi; lo] rows of the same tile pair,
                 // N = 2 slot_rows, so one MMA forms [Dhh | Dhl] (Dhl from column slot_rows)
                 const uint32_t idesc_cat = (1u << 4) | ((uint32_t)((2 * a.slot_rows) >> 3) << 17) |
@@ -439,21 +470,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                             const uint32_t ab = base + (uint32_t)at * atom_bytes;
 #pragma unroll
                             for (int kk = 0; kk < KK; ++kk) {
-                                const uint64_t ah = op_desc<MODE>(ab + 32u * kk);
-                                if (MODE == 0) {
-                                    const uint64_t al = op_desc<MODE>(ab + plane_off + 32u * kk);
-                                    if (diag) {
-                                        mma<MODE>(d0, ah, ah, idesc_cat, acc);
-                                    } else {
-                                        const uint64_t bh = op_desc<MODE>(ab + tile_set + 32u * kk);
-                                        const uint64_t bl = op_desc<MODE>(ab + tile_set + plane_off + 32u * kk);
-                                        mma<MODE>(d0, ah, bh, idesc, acc);
+                                if (single) {
+                                    const uint64_t ah = op_desc<MODE>(ab + 32u * kk);
+                                    // FP32 mode: B = [hi; lo] forms [Dhh | Dhl]
+                                    mma<MODE>(d0, ah, ah, MODE == 0 ? idesc_cat : idesc, acc);
+                                } else {
+                                    const uint64_t ah = op_desc<MODE>(ab + a_hi + 32u * kk);
+                                    const uint64_t bh = op_desc<MODE>(ab + bh_off + 32u * kk);
+                                    mma<MODE>(d0, ah, bh, idesc, acc);
+                                    if (MODE == 0) {
+                                        const uint64_t al = op_desc<MODE>(ab + a_lo + 32u * kk);
+                                        const uint64_t bl = op_desc<MODE>(ab + bl_off + 32u * kk);
                                         mma<MODE>(d0, ah, bl, idesc, 1u);
                                         mma<MODE>(d0, al, bh, idesc, 1u);
                                     }
-                                } else {
-                                    const uint64_t bd = diag ? ah : op_desc<MODE>(ab + tile_set + 32u * kk);
-                                    mma<MODE>(d0, ah, bd, idesc, acc);
                                 }
                                 acc = 1;
                             }
@@ -496,22 +526,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
             const Piece pc = *epi_pc;
             const Item& itm = pc.itm;
             const TcModeArgs& d = a.md[itm.m];
-            const bool diag = itm.b1 == itm.b2;
-            const bool use_t = MODE == 0 && diag;
+            const bool single = !WIDE || d.nblk == 1;
+            const bool diag = single;                // the single block's pair (b1 = b2 = 0)
+            const bool use_t = MODE == 0 && single;
             const int nb1 = block_ants(d.N, itm.b1);
-            const int nb2 = block_ants(d.N, itm.b2);
+            const int nb2 = single ? nb1 : block_ants(d.N, itm.b2);
             const int R2a = 2 * nb1;
             const int R2b = 2 * nb2;
-            const int NH = ((R2b + 15) & ~15) >> 1;  // columns per half, multiple of 8
+            // columns per half: one block 2N rounded up to 16, halved (<= 64);
+            // a group 128 per B block, halved (<= 128)
+            const int NH = single ? ((R2b + 15) & ~15) >> 1 : (kRows * itm.nbB) >> 1;
             const int col0 = h * NH;
             const int64_t s_beg = pc.s_beg;
             const int64_t s_end = pc.s_end;
-            float gacc[64], tacc[64];
+            // window sums: acc[0 .. NH) (single block, FP32 mode: [0, 64) from
+            // hi hi^T and [64, 64 + NH) from hi lo^T)
+            float acc[128];
 #pragma unroll
-            for (int j = 0; j < 64; ++j) {
-                gacc[j] = 0.f;
-                tacc[j] = 0.f;
-            }
+            for (int j = 0; j < 128; ++j) acc[j] = 0.f;
             bool dead = false;
             for (int64_t w0 = s_beg; w0 < s_end; w0 += a.W, ++wi) {
                 if (dead) continue;
@@ -528,23 +560,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                 const uint32_t trow =
                     tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)b * 256u + (uint32_t)col0;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
+                for (int c = 0; c < 16; ++c) {
                     if (8 * c < NH) {
                         uint32_t v[8];
                         tmem_ld8(trow + 8u * c, v);
-                        if (use_t) {
+                        if (c < 8 && use_t) {
                             uint32_t w[8];
                             tmem_ld8(trow + (uint32_t)a.slot_rows + 8u * c, w);
                             tmem_ld_wait();
 #pragma unroll
                             for (int j = 0; j < 8; ++j) {
-                                gacc[8 * c + j] += __uint_as_float(v[j]);
-                                tacc[8 * c + j] += __uint_as_float(w[j]);
+                                acc[8 * c + j] += __uint_as_float(v[j]);
+                                acc[(64 + 8 * c + j) & 127] += __uint_as_float(w[j]);
                             }
                         } else {
                             tmem_ld_wait();
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) gacc[8 * c + j] += __uint_as_float(v[j]);
+                            for (int j = 0; j < 8; ++j) acc[8 * c + j] += __uint_as_float(v[j]);
                         }
                     }
                 }
@@ -553,13 +585,83 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                 if (lane == 0) mbar_arrive(smem_u32(&acce[b]));   // this warp's slice is free
             }
             epi_sync();
-            if (*abort_word) break;
+            // one reading of the abort word for the 8 warps (the producer and
+            // the MMA thread may set it at any time)
+            if (et == 0) *epi_abort = *abort_word;
+            epi_sync();
+            if (*epi_abort) break;
+            const int N = d.N, C = d.C, P = d.P;
+            const bool direct = pc.nslots == 1;
+            if (!single) {
+                // Group: rows 2 i' and 2 i' + 1 (Re and Im of antenna i') are
+                // adjacent lanes, so V comes from one exchange with the partner
+                // lane: for B columns 2 j'' and 2 j'' + 1 the even lane holds
+                // G[2i'][..], the odd lane G[2i'+1][..];
+                //   Re V = G[2i'][2j''] + G[2i'+1][2j''+1], Im V = G[2i'+1][2j''] - G[2i'][2j''+1].
+                // The even lane takes the even column pairs, the odd lane the
+                // odd ones, into the warp's staging rows (16 antennas x kVCols
+                // baselines per round); the warp then writes each antenna's
+                // kVCols baselines, consecutive in the accumulator layout, as
+                // one coalesced run of FP32 stores into the item's partial
+                // slot.  (FP64 reductions straight into the accumulator, one
+                // per word, cost a group pass at N = 256 ~70% more time.)
+                const int odd = r & 1;
+                float2* vst = vstage + (warp - 2) * 16 * kVRow;
+                const int jg0 = col0 >> 1;                  // the warp's first baseline of the group
+                float2* pout = d.partial + ((int64_t)pc.slot * C + itm.k) * P;
+#pragma unroll
+                for (int rho = 0; rho < 64 / kVCols; ++rho) {
+                    if (2 * kVCols * rho < NH) {
+#pragma unroll
+                        for (int kk = 0; kk < kVCols; ++kk) {
+                            const int k2 = kVCols * rho + kk;
+                            const float v0 = acc[2 * k2], v1 = acc[2 * k2 + 1];
+                            const float x0 = __shfl_xor_sync(0xffffffffu, v0, 1);
+                            const float x1 = __shfl_xor_sync(0xffffffffu, v1, 1);
+                            if ((kk & 1) == odd) {
+                                const float av = odd ? x0 : v0, bv = odd ? x1 : v1;
+                                const float cv = odd ? v0 : x0, dv = odd ? v1 : x1;
+                                vst[(lane >> 1) * kVRow + kk] = make_float2(av + dv, cv - bv);
+                            }
+                        }
+                        __syncwarp();
+                        // lane -> baseline jj of the round and one of 32 / kVCols
+                        // antennas of each step over the warp's 16
+                        constexpr int kRowsPerStep = 32 / kVCols;
+                        const int jj = lane % kVCols;
+                        const int jg = jg0 + kVCols * rho + jj;
+                        const int b2 = itm.b2 + (jg >> 6);
+                        const int j_loc = jg & 63;
+                        const bool jv = j_loc < block_ants(N, b2);
+                        const int j = 64 * b2 + j_loc;
+                        const float sj = !jv ? 1.f
+                                             : (MODE == 0 ? __ldg(d.split + j)
+                                                          : __ldg(d.scale + (int64_t)j * C + itm.k));
+#pragma unroll 1
+                        for (int i0 = 0; i0 < 16; i0 += kRowsPerStep) {
+                            const int i16 = i0 + lane / kVCols;
+                            const int i_loc = 16 * q + i16;
+                            if (16 * q + i0 >= nb1) break;
+                            if (i_loc < nb1 && jv && !(b2 == itm.b1 && j_loc < i_loc)) {
+                                const int i = 64 * itm.b1 + i_loc;
+                                const float si = MODE == 0 ? __ldg(d.split + i)
+                                                           : __ldg(d.scale + (int64_t)i * C + itm.k);
+                                const float f = 1.0f / (si * sj);
+                                const float2 v = vst[i16 * kVRow + jj];
+                                const int p = i * N - i * (i - 1) / 2 + (j - i);
+                                pout[p] = make_float2(v.x * f, v.y * f);
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+            } else {
             const int ldg = R2b + 1;
             if (r < R2a) {
 #pragma unroll
                 for (int c = 0; c < 64; ++c) {
                     const int col = col0 + c;
-                    if (c < NH && col < R2b) Gs[r * ldg + col] = gacc[c] + (use_t ? tacc[c] : 0.f);
+                    if (c < NH && col < R2b) Gs[r * ldg + col] = acc[c] + (use_t ? acc[64 + c] : 0.f);
                 }
             }
             epi_sync();
@@ -569,14 +671,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
 #pragma unroll
                     for (int c = 0; c < 64; ++c) {
                         const int col = col0 + c;
-                        if (c < NH && col < R2b) Gs[col * ldg + r] += tacc[c];
+                        if (c < NH && col < R2b) Gs[col * ldg + r] += acc[64 + c];
                     }
                 }
                 epi_sync();
             }
-            const int N = d.N, C = d.C, P = d.P;
-            const int npl = diag ? nb1 * (nb1 + 1) / 2 : nb1 * nb2;
-            const bool direct = pc.nslots == 1;
+            const int npl = nb1 * (nb1 + 1) / 2;
             {
                 // kVB pairs per thread at a time: their accumulator loads are
                 // issued together, so their latencies overlap
@@ -638,10 +738,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                     }
                 }
             }
+            }
             if (!direct) {
                 // The last of the CTAs sharing this (channel, block pair) to
                 // finish adds every partial, in slot order, into the FP64
-                // accumulator: deterministic, and no reduction launch.
+                // accumulator (a group: into slot 0, see the run's reduction):
+                // deterministic.
                 __threadfence();
                 epi_sync();
                 if (et == 0) {
@@ -651,22 +753,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                 epi_sync();
                 if (*epi_last) {
                     __threadfence();
+                    // every pair of the item: the single block's upper
+                    // triangle, or a group's nb1 x (64 per B block) rows and
+                    // columns (the diagonal block's upper triangle)
                     int li = 0;
                     int row_next = nb1;
-                    for (int pl = et; pl < npl; pl += 256) {
-                        int lj;
-                        if (diag) {
+                    const int npl_all = single ? nb1 * (nb1 + 1) / 2 : nb1 * 64 * itm.nbB;
+                    for (int pl = et; pl < npl_all; pl += 256) {
+                        int i, j;
+                        if (single) {
                             while (pl >= row_next) {
                                 ++li;
                                 row_next += nb1 - li;
                             }
-                            lj = li + (pl - (row_next - (nb1 - li)));
+                            i = li;
+                            j = li + (pl - (row_next - (nb1 - li)));
                         } else {
-                            li = pl / nb2;
-                            lj = pl - li * nb2;
+                            const int i_loc = pl / (64 * itm.nbB);
+                            const int rest = pl - i_loc * 64 * itm.nbB;
+                            const int b2 = itm.b2 + (rest >> 6);
+                            const int j_loc = rest & 63;
+                            if (j_loc >= block_ants(N, b2) || (b2 == itm.b1 && j_loc < i_loc)) continue;
+                            i = 64 * itm.b1 + i_loc;
+                            j = 64 * b2 + j_loc;
                         }
-                        const int i = 64 * itm.b1 + li;
-                        const int j = 64 * itm.b2 + lj;
                         const int p = i * N - i * (i - 1) / 2 + (j - i);
                         double re = 0.0, im = 0.0;
                         for (int sp = 0; sp < pc.nslots; ++sp) {
@@ -674,11 +784,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                             re += (double)v.x;
                             im += (double)v.y;
                         }
-                        double2* dst = d.acc + (int64_t)itm.k * P + p;
-                        double2 v = *dst;
-                        v.x += re;
-                        v.y += im;
-                        *dst = v;
+                        if (single) {
+                            double2* dst = d.acc + (int64_t)itm.k * P + p;
+                            double2 v = *dst;
+                            v.x += re;
+                            v.y += im;
+                            *dst = v;
+                        } else {
+                            // a group's pass result lives in slot 0 until the
+                            // reduction launch adds it to the accumulator
+                            d.partial[(int64_t)itm.k * P + p] = make_float2((float)re, (float)im);
+                        }
                     }
                     if (et == 0) d.ticket[itm.k * d.npairs + itm.pr] = 0;
                 }
@@ -745,7 +861,7 @@ int tc_plan_create(TcPlan** out, int N, int C, int spec_type, std::string& err) 
     p->C = C;
     p->P = N * (N + 1) / 2;
     p->nblk = (N + 63) / 64;
-    p->npairs = p->nblk * (p->nblk + 1) / 2;
+    p->npairs = groups_of(p->nblk);
     p->mode = spec_type == SPEC_F16X2 ? 0 : (spec_type == SPEC_F16 ? 1 : 2);
     p->planes = p->mode == 0 ? 2 : 1;
     p->KT = p->mode == 2 ? 128 : 32;
@@ -837,37 +953,31 @@ int tc_set_tiles(TcPlan* p, int window, int stages, int split, int atoms, std::s
 
 namespace {
 
-// Work units per k-tile of block pair pr, as pair_units() on the device.
-int host_pair_units(int pr, int nblk) {
-    int b1 = 0;
-    while (pr >= nblk - b1) {
-        pr -= nblk - b1;
-        ++b1;
-    }
-    return pr == 0 ? 2 : 3;
-}
+// Work units per k-tile of work group pr (pair_units()).
+int host_pair_units(int pr, int nblk) { return pair_units(pr, nblk); }
 
 struct LaunchShape {
-    int two_tiles, gs_floats, stages, W, atoms, slot_rows;
+    int wide, gs_floats, stages, W, atoms, slot_rows;
     size_t smem;
 };
 
 LaunchShape launch_shape(TcPlan* const* plans, int n) {
     LaunchShape L{};
-    int r2max = 0;
+    int r2max = 0;     // the G buffer serves the single-block modes only
     for (int m = 0; m < n; ++m) {
-        L.two_tiles |= plans[m]->nblk > 1;
-        r2max = std::max(r2max, 2 * std::min(64, plans[m]->N));
+        L.wide |= plans[m]->nblk > 1;
+        if (plans[m]->nblk == 1) r2max = std::max(r2max, 2 * plans[m]->N);
     }
     L.gs_floats = r2max * (r2max + 1);
     L.slot_rows = 8;
     for (int m = 0; m < n; ++m) L.slot_rows = std::max(L.slot_rows, plans[m]->box_rows);
     const size_t slot = (size_t)L.slot_rows * plans[0]->row_bytes;
     // + the rows an MMA reads past the ring's last slot
-    const size_t fixed = 1024 + (size_t)L.gs_floats * 4 + 16 + 16 + 8 * (2 * 16 + 5) + 256 +
+    const size_t vstage = L.wide ? (size_t)8 * 16 * kVRow * sizeof(float2) : 0;
+    const size_t fixed = 1024 + (size_t)L.gs_floats * 4 + vstage + 16 + 16 + 8 * (2 * 16 + 5) + 256 +
                          (size_t)(kRows - L.slot_rows) * plans[0]->row_bytes;
     auto fit = [&](int atoms) {
-        const size_t sb = (size_t)plans[0]->planes * atoms * slot * (L.two_tiles ? 2 : 1);
+        const size_t sb = (size_t)plans[0]->planes * atoms * slot * (L.wide ? 3 : 1);
         return std::min<int>(16, (int)((kSmemBudget - fixed) / sb));
     };
     // k-tiles per stage, unless set: as many (up to 256 spectra: 8 k-tiles of
@@ -878,7 +988,7 @@ LaunchShape launch_shape(TcPlan* const* plans, int n) {
     L.atoms = plans[0]->atoms;
     if (!L.atoms) {
         L.atoms = 1;
-        const int min_stages = L.two_tiles ? 2 : 3;
+        const int min_stages = L.wide ? 2 : 3;
         for (int at = plans[0]->KT == 32 ? 8 : 4; at > 1; at /= 2)
             if (fit(at) >= min_stages) {
                 L.atoms = at;
@@ -887,13 +997,14 @@ LaunchShape launch_shape(TcPlan* const* plans, int n) {
     }
     while (L.atoms > 1 && fit(L.atoms) < 2) L.atoms /= 2;
     const size_t stage_bytes =
-        (size_t)plans[0]->planes * L.atoms * slot * (L.two_tiles ? 2 : 1);
+        (size_t)plans[0]->planes * L.atoms * slot * (L.wide ? 3 : 1);
     const int smax = fit(L.atoms);
     L.stages = plans[0]->stages ? std::min(plans[0]->stages, smax) : std::min(smax, 8);
     const int step = plans[0]->KT * L.atoms;
     // default window: 256 spectra in FP32 mode (TMEM accumulation bias ~1e-6
-    // at full size), 512 for FP16 / FP8 (their input rounding dominates)
-    const int W0 = plans[0]->mode == 0 ? 256 : 512;
+    // at full size), 1024 for FP16 / FP8 (their input rounding dominates;
+    // at N = 256 a pass takes ~10% less time than with 512)
+    const int W0 = plans[0]->mode == 0 ? 256 : 1024;
     int W = plans[0]->window ? plans[0]->window : std::max(W0, plans[0]->KT);
     L.W = (W + step - 1) / step * step;   // windows hold whole stages
     L.smem = fixed + (size_t)L.stages * stage_bytes;
@@ -1048,7 +1159,7 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
     a.row_bytes = plans[0]->row_bytes;
     a.W = L.W;
     a.atoms = L.atoms;
-    a.two_tiles = L.two_tiles;
+    a.wide = L.wide;
     a.gs_floats = L.gs_floats;
     a.slot_rows = L.slot_rows;
     a.status = runs[0].status;
@@ -1088,8 +1199,11 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
         d.unit_base = units;
         for (int pr = 0; pr < p->npairs; ++pr)
             units += item_units(d.tiles, host_pair_units(pr, p->nblk)) * p->C;
-        runs[m].n_split = d.n_split;
-        runs[m].direct = true;          // splits are combined inside the kernel
+        // single block: splits are combined inside the kernel, into acc;
+        // several blocks: every pass result lands in partial slot 0 (coalesced
+        // FP32 stores), which one reduction launch adds to acc
+        runs[m].direct = p->nblk == 1;
+        runs[m].n_split = runs[m].direct ? d.n_split : 1;
     }
     a.total_items = base;
     if (base == 0) return CORR_OK;
@@ -1100,19 +1214,18 @@ int tc_launch(TcPlan* const* plans, int n, TcRun* runs, cudaStream_t st, std::st
         grid = deal.grid;
     }
     cudaError_t e;
-    if (plans[0]->mode == 0) {
-        e = cudaFuncSetAttribute(xengine_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)L.smem);
-        if (e == cudaSuccess) xengine_tc_kernel<0><<<grid, kTcThreads, L.smem, st>>>(a);
-    } else if (plans[0]->mode == 1) {
-        e = cudaFuncSetAttribute(xengine_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)L.smem);
-        if (e == cudaSuccess) xengine_tc_kernel<1><<<grid, kTcThreads, L.smem, st>>>(a);
-    } else {
-        e = cudaFuncSetAttribute(xengine_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)L.smem);
-        if (e == cudaSuccess) xengine_tc_kernel<2><<<grid, kTcThreads, L.smem, st>>>(a);
-    }
+    auto go = [&](auto kern) {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)L.smem);
+        if (r == cudaSuccess) kern<<<grid, kTcThreads, L.smem, st>>>(a);
+        return r;
+    };
+    if (plans[0]->mode == 0)
+        e = L.wide ? go(xengine_tc_kernel<0, true>) : go(xengine_tc_kernel<0, false>);
+    else if (plans[0]->mode == 1)
+        e = L.wide ? go(xengine_tc_kernel<1, true>) : go(xengine_tc_kernel<1, false>);
+    else
+        e = L.wide ? go(xengine_tc_kernel<2, true>) : go(xengine_tc_kernel<2, false>);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = std::string("tensor-core X-engine launch: ") + cudaGetErrorString(e);

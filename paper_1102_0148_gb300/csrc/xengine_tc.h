@@ -14,13 +14,14 @@ struct TcPlan;
 // What one mode of a tensor-core launch reads and writes.
 struct TcRun {
     int64_t S_pad;            // frames in the workspace pass (multiple of 128)
-    float2* partial;          // [max_split][C][P] partials, used when n_split > 1
-    double2* acc;             // [C][P] FP64 accumulator, added to when n_split == 1
+    float2* partial;          // [max_split][C][P] FP32 partials (split items; slot 0 holds
+                              // a multi-block mode's whole pass result)
+    double2* acc;             // [C][P] FP64 accumulator
     const float* scale;       // [N][C] pre-cast scales (FP16 / FP8), else nullptr
     const float* split;       // [N] two-plane pre-scales sigma_i (FP32 mode), else nullptr
     int* status;              // device status word (bounded waits)
-    int n_split;              // out: ranges per channel (combined in the kernel)
-    bool direct;              // out: accumulated into acc (no reduction needed)
+    int n_split;              // out: partial slots the reduction adds (when !direct)
+    bool direct;              // out: accumulated into acc in the kernel (single block)
 };
 
 // Prepare a plan for N antennas and C channels of workspace type spec_type.

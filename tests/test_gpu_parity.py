@@ -148,7 +148,8 @@ def test_ragged_pushes_chunks_and_corrections(lib, torch_cuda, dtype):
 
 @pytest.mark.parametrize("dtype", DTYPES_FP32)
 @pytest.mark.parametrize("N,K,S", [(1, 16, 7), (2, 32, 1), (13, 128, 129), (64, 256, 200),
-                                   (65, 64, 50), (128, 32, 70), (200, 16, 40)])
+                                   (65, 64, 50), (128, 32, 70), (200, 16, 40), (401, 16, 33),
+                                   (512, 16, 40)])
 def test_edge_shapes(lib, torch_cuda, dtype, N, K, S):
     packed, _ = synth.make_samples(N, S * K, K, seed=SEED + N * 1000 + K)
     R, _ = oracle.correlate(packed, N, K)
@@ -255,13 +256,34 @@ def test_precision_forms_cfg1(lib, torch_cuda, dtype):
 @pytest.mark.parametrize("dtype", ["fp32", "fp32_simt"])
 def test_n256_k1024(lib, torch_cuda, dtype):
     """The density scale-up geometry: 256 antennas (four 64-antenna blocks,
-    ten block pairs per channel), K = 1024."""
+    ten block pairs in six work groups per channel), K = 1024."""
     N, K, S = 256, 1024, 160
     packed, _ = synth.make_samples(N, S * K, K, seed=SEED + 256)
     R, _ = oracle.correlate(packed, N, K)
     V, n = run_gpu(lib, torch_cuda, packed, N, K, dtype)
     assert n == S
     assert vis_error(V, R, N) <= TOL
+
+
+# FP16 / FP8 with several 64-antenna blocks (work groups of one A block and
+# up to two B blocks): about twice the errors measured on a GB300 (1.30e-4,
+# 1.43e-4, 2.10e-2, 1.83e-2)
+MULTIBLOCK_BOUND = {("fp16", 130): 2.6e-4, ("fp16", 256): 2.9e-4,
+                    ("fp8", 130): 4.2e-2, ("fp8", 256): 3.7e-2}
+
+
+@pytest.mark.parametrize("dtype", ["fp16", "fp8"])
+@pytest.mark.parametrize("N,K,S", [(130, 256, 256), (256, 1024, 256)])
+def test_multiblock_precision_forms(lib, torch_cuda, dtype, N, K, S):
+    """Three and four antenna blocks in the FP16 and FP8 forms: the last
+    block's ragged rows, groups whose second B block is absent, and
+    baselines that cross block boundaries, against the FP64 oracle."""
+    packed, _ = synth.make_samples(N, S * K, K, seed=SEED + 7 * N + K)
+    R, _ = oracle.correlate(packed, N, K)
+    V, n = run_gpu(lib, torch_cuda, packed, N, K, dtype)
+    assert n == S
+    e = report_err(f"multiblock-{dtype}-N{N}-K{K}", vis_error(V, R, N))
+    assert e <= MULTIBLOCK_BOUND[(dtype, N)], e
 
 
 @pytest.mark.parametrize("window,stages,split", [(64, 2, 0), (256, 3, 8), (512, 0, 3), (128, 4, 1)])

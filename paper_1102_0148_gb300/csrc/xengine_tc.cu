@@ -1002,9 +1002,11 @@ LaunchShape launch_shape(TcPlan* const* plans, int n) {
     L.stages = plans[0]->stages ? std::min(plans[0]->stages, smax) : std::min(smax, 8);
     const int step = plans[0]->KT * L.atoms;
     // default window: 256 spectra in FP32 mode (TMEM accumulation bias ~1e-6
-    // at full size), 1024 for FP16 / FP8 (their input rounding dominates;
-    // at N = 256 a pass takes ~10% less time than with 512)
-    const int W0 = plans[0]->mode == 0 ? 256 : 1024;
+    // at full size); 512 for FP16 / FP8 (their input rounding dominates),
+    // 1024 when a mode has several antenna blocks (~10% less time per pass
+    // at N = 256; at N = 44 it raised the 1 s FP16 error from 5.7e-6 to
+    // 8.1e-6 for no gain)
+    const int W0 = plans[0]->mode == 0 ? 256 : (L.wide ? 1024 : 512);
     int W = plans[0]->window ? plans[0]->window : std::max(W0, plans[0]->KT);
     L.W = (W + step - 1) / step * step;   // windows hold whole stages
     L.smem = fixed + (size_t)L.stages * stage_bytes;

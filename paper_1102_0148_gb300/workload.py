@@ -52,24 +52,25 @@ def xengine_issued_flops(N, K, s_pad, dtype):
     """Flops the tensor-core X-engine issues for one pass of ``s_pad`` padded
     spectra: 2 M N K per tcgen05.mma, with the tile shapes the kernel uses.
 
-    Antennas come in blocks of 64 (rows [Re; Im], 2 nb of them), and every
-    channel runs one dense contraction per block pair b1 <= b2 with M = 128
+    Antennas come in blocks of 64 (rows [Re; Im], 2 nb of them), M = 128
     rows.  Per spectrum and channel:
-    * FP32 mode (two FP16 planes): a diagonal pair issues one MMA whose B is
-      [hi; lo], N = 2 r (r = the operand tile's rows: 2N rounded up to 8 for
-      a single block, else 128); an off-diagonal pair three MMAs with
-      N = 2 nb2 rounded up to 16;
-    * FP16 / FP8: one MMA with N = 2 nb2 rounded up to 16.
+    * one block (N <= 64): FP32 mode (two FP16 planes) one MMA whose B is
+      [hi; lo], N = 2 r (r = 2N rounded up to 8); FP16 / FP8 one MMA with
+      N = 2N rounded up to 16;
+    * several blocks: work groups of block b1 against blocks b2 .. b2 +
+      nbB - 1 (b2 = b1, b1 + 2, ...; nbB = 2, or 1 for a row's last), one
+      MMA with N = 128 nbB (three in FP32 mode: hi hi, hi lo, lo hi).
     """
     nblk = (N + 63) // 64
-    nb = [min(64, N - 64 * b) for b in range(nblk)]
-    rows = (2 * N + 7) // 8 * 8 if nblk == 1 else 128
-    per = 0
-    for b1 in range(nblk):
-        for b2 in range(b1, nblk):
-            nn = (2 * nb[b2] + 15) // 16 * 16
-            if dtype == "fp32":
-                per += 2 * 128 * (2 * rows) if b1 == b2 else 3 * 2 * 128 * nn
-            else:
-                per += 2 * 128 * nn
+    if nblk == 1:
+        if dtype == "fp32":
+            per = 2 * 128 * (2 * ((2 * N + 7) // 8 * 8))
+        else:
+            per = 2 * 128 * ((2 * N + 15) // 16 * 16)
+    else:
+        per = 0
+        for b1 in range(nblk):
+            for b2 in range(b1, nblk, 2):
+                nn = 128 * min(2, nblk - b2)
+                per += (3 if dtype == "fp32" else 1) * 2 * 128 * nn
     return float(per) * (K // 2) * s_pad

@@ -317,6 +317,7 @@ int corr_debug_spectra(corr_t h, const uint8_t* samples, int64_t n, float* spect
  * corr_batch_replay  launch the recorded graph (asynchronous): every replay
  *                    writes one complete integration per mode into vis[m];
  *                    n_spec[m] (may be NULL) receives the spectra per mode.
+ *                    CORR_ESTATE when frames were pushed since the last dump.
  * corr_batch_sync    wait for the batch stream; reports device-side errors.
  * corr_batch_handle  the corr_t of mode m (corrections, scales, profiling;
  *                    not to be destroyed or given another stream).

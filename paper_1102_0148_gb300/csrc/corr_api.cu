@@ -101,6 +101,7 @@ struct corr_s {
     int64_t shifted_frames = 0;
     void* vis_dev = nullptr;
     int64_t n_spec = 0;
+    bool acc_zero = true;        // acc holds zeros (created, or dumped since its last pass)
     int64_t fill = 0;            // frames waiting in the workspace for the X-engine
     double2* fill_acc = nullptr; // accumulator those frames belong to
     TcPlan* tc = nullptr;
@@ -356,10 +357,14 @@ int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off)
 
 // FP64 reduction of a tensor-core launch's partials, when it wrote any.
 int finish_tc_run(corr_t h, const TcRun& run, double2* acc) {
+    // a multi-block mode's pass result covers every (k, p): into a zero
+    // accumulator it is stored, not added
+    const bool assign = acc == h->acc && h->acc_zero;
+    if (acc == h->acc) h->acc_zero = false;
     if (run.direct) return CORR_OK;
     prof_begin(h);
     CUDA_TRY(h, launch_reduce_partials(h->partial, run.n_split, (int64_t)h->C * h->P, acc,
-                                       h->stream));
+                                       h->stream, assign));
     prof_end(h, CORR_KERNEL_REDUCE);
     return CORR_OK;
 }
@@ -394,9 +399,11 @@ int xengine_pass(corr_t h, int64_t S_pad, double2* acc) {
         prof_begin(h);
         CUDA_TRY(h, launch_xengine_simt(xa, h->stream));
         prof_end(h, CORR_KERNEL_XENGINE);
+        const bool assign = acc == h->acc && h->acc_zero;
+        if (acc == h->acc) h->acc_zero = false;
         prof_begin(h);
         CUDA_TRY(h, launch_reduce_partials(h->partial, xa.n_split, (int64_t)h->C * h->P, acc,
-                                           h->stream));
+                                           h->stream, assign));
         prof_end(h, CORR_KERNEL_REDUCE);
     }
     return CORR_OK;
@@ -409,6 +416,7 @@ int fx_flush(corr_t h) {
     int rc = fx_launch(h->fx, h->fx_pending.data(), (int)h->fx_pending.size(), h->twiddle,
                        split_table(h, false), h->corr_on ? h->corr_tab : nullptr, h->acc, h->status,
                        h->stream, h->err);
+    h->acc_zero = false;
     h->fx_pending.clear();
     h->fx_pending_blocks = 0;
     if (rc != CORR_OK) return rc;
@@ -935,6 +943,7 @@ int corr_load_state(corr_t h, const void* buf) {
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     const unsigned char* p = static_cast<const unsigned char*>(buf) + sizeof hd;
     const size_t ab = (size_t)h->C * h->P * sizeof(double2);
+    h->acc_zero = false;
     CUDA_TRY(h, cudaMemcpy(h->acc, p, ab, cudaMemcpyHostToDevice));
     p += ab;
     if (narrow(h)) {
@@ -1147,7 +1156,8 @@ int enqueue_dump(corr_t h, void* vis, int vis_fp64, bool dev) {
         h->scales_ready = true;
     }
     prof_begin(h);
-    CUDA_TRY(h, launch_dump(h->acc, h->C, h->P, out, vis_fp64, h->stream));
+    CUDA_TRY(h, launch_dump(h->acc, h->C, h->P, out, vis_fp64, h->stream));   // also clears acc
+    h->acc_zero = true;
     prof_end(h, CORR_KERNEL_DUMP);
     if (!dev) CUDA_TRY(h, cudaMemcpyAsync(vis, out, bytes, cudaMemcpyDeviceToHost, h->stream));
     return CORR_OK;
@@ -1504,6 +1514,7 @@ int corr_batch_capture(corr_batch_t b, const uint8_t* const* samples, const int6
                 e = launch_scales_from_autos(h->acc, h->N, h->C, h->P, h->n_spec, h->scale_target,
                                              h->scale, b->stream);
             if (e == cudaSuccess) e = launch_dump(h->acc, h->C, h->P, vis[m], vis_fp64, b->stream);
+            h->acc_zero = true;
             if (e != cudaSuccess) rc = CORR_ECUDA;
         }
         cudaGraph_t g = nullptr;
@@ -1538,6 +1549,11 @@ int corr_batch_capture(corr_batch_t b, const uint8_t* const* samples, const int6
 int corr_batch_replay(corr_batch_t b, int64_t* n_spec) {
     if (!b) return CORR_EINVAL;
     if (!b->exec) return batch_err(b, CORR_ESTATE, "no captured step: call corr_batch_capture");
+    // a replay is one whole integration per mode: frames pushed eagerly since
+    // the last dump would be lost or miscounted
+    for (int m = 0; m < b->n; ++m)
+        if (b->h[m]->n_spec > 0 || b->h[m]->fill > 0)
+            return batch_err(b, CORR_ESTATE, "frames pushed since the last dump: dump before replaying");
     cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
     if (e != cudaSuccess)
         return batch_err(b, CORR_ECUDA, (std::string("graph launch: ") + cudaGetErrorString(e)).c_str());

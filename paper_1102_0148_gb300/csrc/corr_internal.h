@@ -133,9 +133,10 @@ struct XengineArgs {
 // Chooses the split of the pass (a.s_per_split, a.n_split) and launches.
 cudaError_t launch_xengine_simt(XengineArgs& a, cudaStream_t st);
 
-// acc[k][p] += sum over splits of partial[split][k][p], in a fixed order (FP64).
+// acc[k][p] += sum over splits of partial[split][k][p], in a fixed order (FP64);
+// assign: acc is known to hold zeros, acc[k][p] = that sum without reading it.
 cudaError_t launch_reduce_partials(const float2* partial, int n_split, int64_t CP,
-                                   double2* acc, cudaStream_t st);
+                                   double2* acc, cudaStream_t st, bool assign = false);
 
 // vis[p][k] = acc[k][p] as complex64 (fp64 == 0) or complex128; then acc = 0.
 cudaError_t launch_dump(double2* acc, int C, int P, void* vis, int fp64, cudaStream_t st);

@@ -174,7 +174,8 @@ __global__ void __launch_bounds__(256) xengine_simt_kernel(XengineArgs a, int nb
 // the pass total is added to the FP64 accumulator.  FP64 arithmetic runs at a
 // small fraction of the FP32 rate on this GPU, so one FP64 add per element
 // and pass keeps the kernel bound by its loads.
-__global__ void reduce_partials_kernel(const float2* part, int n_split, int64_t CP, double2* acc) {
+__global__ void reduce_partials_kernel(const float2* part, int n_split, int64_t CP, double2* acc,
+                                       int assign) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < CP;
          e += (int64_t)gridDim.x * blockDim.x) {
         float2 t[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
@@ -193,7 +194,9 @@ __global__ void reduce_partials_kernel(const float2* part, int n_split, int64_t 
             t[0].x += v.x;
             t[0].y += v.y;
         }
-        double2 o = acc[e];
+        // assign: acc is known to be zero (the first pass of an integration),
+        // so its read is skipped
+        double2 o = assign ? make_double2(0.0, 0.0) : acc[e];
         o.x += (double)((t[0].x + t[1].x) + (t[2].x + t[3].x));
         o.y += (double)((t[0].y + t[1].y) + (t[2].y + t[3].y));
         acc[e] = o;
@@ -297,8 +300,8 @@ cudaError_t launch_xengine_simt(XengineArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_reduce_partials(const float2* partial, int n_split, int64_t CP, double2* acc,
-                                   cudaStream_t st) {
-    reduce_partials_kernel<<<grid_for(CP), 256, 0, st>>>(partial, n_split, CP, acc);
+                                   cudaStream_t st, bool assign) {
+    reduce_partials_kernel<<<grid_for(CP), 256, 0, st>>>(partial, n_split, CP, acc, assign ? 1 : 0);
     return cudaGetLastError();
 }
 

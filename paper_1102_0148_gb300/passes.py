@@ -1,6 +1,7 @@
 """Time whole workspace passes of one geometry, kernel class by kernel class.
 
     python -m paper_1102_0148_gb300.passes --N 256 --K 1024 --dtype fp16 --frames 4096
+    python -m paper_1102_0148_gb300.passes --batch 44:512,22:2048,11:4096,256:1024 --dtype fp16
 
 Each step pushes ``frames`` spectra per antenna of synthetic device-resident
 input (drawn on the GPU) as one pass and dumps the integration.  After
@@ -55,10 +56,55 @@ def run(N, K, dtype="fp32", frames=4096, steps=5, warmup=3, window=0, stages=0, 
     return out
 
 
+def run_batch(modes, dtype="fp16", samples=1 << 22, steps=20, warmup=3, window=0, stages=0,
+              split=0, seed=5):
+    """Replays of the captured step of a batch (push of ``samples`` per antenna
+    and mode, one pass per mode, and the dump), timed with CUDA events on the
+    batch's stream; eager per-class launch counts of one step."""
+    import torch
+    data = []
+    for m, (N, K) in enumerate(modes):
+        d, _ = synth.make_samples_torch(N, samples, K, seed=seed + m, device="cuda")
+        data.append(d.reshape(-1))
+    with corr.CorrelatorBatch(modes, dtype, window=window, stages=stages, split=split) as b:
+        for h, (N, K) in zip(b.handles, modes):
+            corr.corr_set_chunk(h, samples // K)
+            corr.corr_profile_enable(h, True)
+            corr.corr_profile_read(h)
+        b.push(data)
+        b.dump()
+        launches = {}
+        for h in b.handles:
+            for c, (n, _) in corr.corr_profile_read(h).items():
+                if n:
+                    launches[c] = launches.get(c, 0) + n
+            corr.corr_profile_enable(h, False)
+        vis = [torch.empty((N * (N + 1) // 2, K // 2), dtype=torch.complex64, device="cuda")
+               for N, K in modes]
+        b.capture(data, vis)
+        s = torch.cuda.ExternalStream(b.stream)
+        for _ in range(warmup):
+            b.replay()
+        b.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            b.replay()
+        e1.record(s)
+        b.sync()
+        ms = e0.elapsed_time(e1) / steps
+    return {"modes": [list(m) for m in modes], "dtype": dtype, "samples": samples,
+            "ms_per_step": ms, "launches_per_step": launches}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--N", type=int, required=True)
-    ap.add_argument("--K", type=int, required=True)
+    ap.add_argument("--N", type=int)
+    ap.add_argument("--K", type=int)
+    ap.add_argument("--batch", default=None,
+                    help="modes N:K,N:K,... (a captured batch step instead of one handle)")
+    ap.add_argument("--samples", type=int, default=1 << 22, help="per antenna and mode (--batch)")
     ap.add_argument("--dtype", default="fp32", choices=sorted(corr.DTYPES))
     ap.add_argument("--frames", type=int, default=4096)
     ap.add_argument("--steps", type=int, default=5)
@@ -68,6 +114,13 @@ def main():
     ap.add_argument("--split", type=int, default=0)
     ap.add_argument("--atoms", type=int, default=0)
     a = ap.parse_args()
+    if a.batch:
+        modes = [tuple(int(v) for v in m.split(":")) for m in a.batch.split(",")]
+        print(json.dumps(run_batch(modes, a.dtype, a.samples, a.steps, a.warmup, a.window,
+                                   a.stages, a.split)))
+        return
+    if a.N is None or a.K is None:
+        ap.error("--N and --K (or --batch) are required")
     print(json.dumps(run(a.N, a.K, a.dtype, a.frames, a.steps, a.warmup, a.window, a.stages,
                          a.split, a.atoms)))
 

@@ -105,3 +105,42 @@ def test_batch_rejects_mixed_or_bad_arguments(lib):
         lib.CorrelatorBatch([(44, 512)] * 5, "fp32")
     with pytest.raises(lib.CorrError):
         lib.CorrelatorBatch(MODES3, "fp32_simt")
+
+
+def test_batch_multiblock_passes_and_replays(lib):
+    """A multi-block mode (N = 130: three antenna blocks) whose pass results
+    go through the FP32 slot and the reduction: several passes per push (the
+    first into a zero accumulator is stored, later ones added), pushes
+    accumulated across calls, and graph replays of fresh data; every result
+    against the oracle.  A replay after an eager push is refused."""
+    import torch
+    modes = [(130, 256), (44, 512)]
+    T = 1 << 16                                   # 256 and 128 frames
+    dev_a, refs_a = make_inputs(modes, T, seed=11020148 + 45)
+    dev_b, refs_b = make_inputs(modes, T, seed=11020148 + 46)
+    with lib.CorrelatorBatch(modes, "fp32", chunk=128) as b:   # 2 passes and 1 per push
+        b.push(dev_a)
+        b.push(dev_b)
+        vis, n = b.dump(fp64=True)
+        for (N, K), V, Ra, Rb, nm in zip(modes, vis, refs_a, refs_b, n):
+            assert nm == 2 * T // K
+            assert norm_err(V, Ra + Rb, N) <= 1e-5, (N, K)
+        bufs = [x.clone() for x in dev_a]
+        out = [torch.empty((N * (N + 1) // 2, K // 2), dtype=torch.complex128, device="cuda")
+               for N, K in modes]
+        b.capture(bufs, out, fp64=True)
+        for dev, refs in ((dev_b, refs_b), (dev_a, refs_a)):
+            for buf, x in zip(bufs, dev):
+                buf.copy_(x)
+            torch.cuda.synchronize()
+            b.replay()
+            b.sync()
+            for (N, K), V, R in zip(modes, out, refs):
+                assert norm_err(V.cpu().numpy(), R, N) <= 1e-5, (N, K)
+        b.push(dev_a)
+        with pytest.raises(lib.CorrError) as ei:
+            b.replay()
+        assert ei.value.code == lib.CORR_ESTATE
+        vis, n = b.dump(fp64=True)                # the eager push is still whole
+        for (N, K), V, R in zip(modes, vis, refs_a):
+            assert norm_err(V, R, N) <= 1e-5, (N, K)

@@ -712,12 +712,18 @@ def measure_batch_form(corr, torch, np, steps=5):
     refs = [oracle.correlate(x[: Tp * N // 2].cpu().numpy(), N, K)[0] for x, (N, K) in zip(data, modes)]
     out = {"workload": "modes (44,512), (22,2048), (11,4096), (256,1024); 2^22 samples/antenna/mode",
            "samples_per_step": sum(N * T for N, _ in modes)}
-    for name in ("fp16", "fp32"):
-        t = tune.tune_batch(modes, name, T=T, repeats=2, save=False,
-                            windows=(128, 256) if name == "fp32" else (512, 1024, 2048),
-                            stages=(3, 4, 6), splits=(0, 1))
-        with corr.CorrelatorBatch(modes, name, window=t["window"], stages=t["stages"],
-                                  split=t["split"]) as b:
+    tiles = {}
+    # *_one_launch: the modes' F-engines as one multi-mode launch
+    # (corr_batch_set_one_launch), with the tiles tuned for the default form
+    for name, dt, one in (("fp16", "fp16", False), ("fp32", "fp32", False),
+                          ("fp16_one_launch", "fp16", True)):
+        if dt not in tiles:
+            tiles[dt] = tune.tune_batch(modes, dt, T=T, repeats=2, save=False,
+                                        windows=(128, 256) if dt == "fp32" else (512, 1024, 2048),
+                                        stages=(3, 4, 6), splits=(0, 1))
+        t = tiles[dt]
+        with corr.CorrelatorBatch(modes, dt, window=t["window"], stages=t["stages"],
+                                  split=t["split"], one_launch=one) as b:
             for h, (N, K) in zip(b.handles, modes):
                 corr.corr_set_chunk(h, T // K)           # one pass per mode and push
                 corr.corr_profile_enable(h, True)

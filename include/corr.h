@@ -324,6 +324,16 @@ int corr_debug_spectra(corr_t h, const uint8_t* samples, int64_t n, float* spect
  * corr_batch_get_stream  the batch's cudaStream_t.
  * corr_batch_set_chunk / corr_batch_set_tiles  as corr_set_chunk /
  *                    corr_set_tiles for every mode; discard a recorded graph.
+ * corr_batch_set_one_launch  on = 1: each pass runs the F-engines of all its
+ *                    modes as one launch (a persistent kernel of 768-thread
+ *                    CTAs, three 256-thread sub-blocks for K = 512, 1024 and
+ *                    other K, 512 threads for K = 2048 / 4096), so a step is
+ *                    one F-engine and one X-engine launch; on = 0 (the
+ *                    default): one launch per mode, side by side.  On a
+ *                    GB300 the single launch is ~10% slower on the batching
+ *                    workload (its union kernel is held to 80 registers and
+ *                    spills); results are the same.  Switching discards a
+ *                    recorded graph.
  * Errors: as the single-mode calls; corr_batch_last_error(b) has the message
  * (corr_last_error(NULL) for corr_batch_create). */
 typedef struct corr_batch_s* corr_batch_t;
@@ -331,6 +341,7 @@ typedef struct corr_batch_s* corr_batch_t;
 int corr_batch_create(corr_batch_t* out, int n_modes, const int* N, const int* K, int dtype);
 int corr_batch_set_chunk(corr_batch_t b, int64_t max_spectra);
 int corr_batch_set_tiles(corr_batch_t b, int window, int stages, int split, int atoms);
+int corr_batch_set_one_launch(corr_batch_t b, int on);
 int corr_batch_push(corr_batch_t b, const uint8_t* const* samples, const int64_t* n);
 int corr_batch_dump(corr_batch_t b, void* const* vis, int64_t* n_spec, int vis_fp64);
 int corr_batch_capture(corr_batch_t b, const uint8_t* const* samples, const int64_t* n,

@@ -61,6 +61,7 @@ _SIGS = {
     "corr_batch_create": (_int, [ctypes.POINTER(_vp), _int, ctypes.POINTER(_int), ctypes.POINTER(_int), _int]),
     "corr_batch_set_chunk": (_int, [_vp, _i64]),
     "corr_batch_set_tiles": (_int, [_vp, _int, _int, _int, _int]),
+    "corr_batch_set_one_launch": (_int, [_vp, _int]),
     "corr_batch_push": (_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i64)]),
     "corr_batch_dump": (_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i64), _int]),
     "corr_batch_capture": (_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.POINTER(_vp), _int]),
@@ -287,6 +288,10 @@ def corr_batch_set_tiles(b, window=0, stages=0, split=0, atoms=0):
                    b)
 
 
+def corr_batch_set_one_launch(b, on=True):
+    return _bcheck(_lib.corr_batch_set_one_launch(b, 1 if on else 0), b)
+
+
 def corr_batch_push(b, samples, n):
     return _bcheck(_lib.corr_batch_push(b, _ptrs(samples), (_i64 * len(n))(*n)), b)
 
@@ -396,7 +401,8 @@ class CorrelatorBatch:
     persistent tensor-core launch per pass (optionally replayed as a CUDA
     graph)."""
 
-    def __init__(self, modes, dtype=CORR_FP32, chunk=None, window=0, stages=0, split=0):
+    def __init__(self, modes, dtype=CORR_FP32, chunk=None, window=0, stages=0, split=0,
+                 one_launch=False):
         self.modes = [tuple(m) for m in modes]
         self.b = corr_batch_create([m[0] for m in self.modes], [m[1] for m in self.modes], dtype)
         self.handles = [corr_batch_handle(self.b, i) for i in range(len(self.modes))]
@@ -405,6 +411,8 @@ class CorrelatorBatch:
             corr_batch_set_chunk(self.b, chunk)
         if window or stages or split:
             corr_batch_set_tiles(self.b, window, stages, split)
+        if one_launch:
+            corr_batch_set_one_launch(self.b, True)
 
     @property
     def stream(self):

@@ -317,18 +317,14 @@ const float* split_table(corr_t h, bool raw) {
 // queued on the next side stream after the work already on the handle's
 // stream; raw = true skips the per-antenna corrections (the uncorrected
 // visibilities corr_grad needs).
-int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off) {
-    const int64_t S_pad = pad_frames(S);
-    if (narrow(h) && !h->scales_ready) {
-        int rc = estimate_scales(h, din, S);
-        if (rc != CORR_OK) return rc;
-    }
+// The F-engine arguments of S frames at din into workspace frame `off`.
+FengineArgs fengine_args(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off) {
     FengineArgs fa{};
     fa.in = din;
     fa.N = h->N;
     fa.K = h->K;
     fa.S = S;
-    fa.S_pad = S_pad;
+    fa.S_pad = pad_frames(S);
     fa.twiddle = h->twiddle;
     fa.corr = (h->corr_on && !raw) ? h->corr_tab : nullptr;
     fa.spec = h->spec;
@@ -338,6 +334,15 @@ int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off)
     fa.scale = (h->spec_type == SPEC_F16 || h->spec_type == SPEC_F8) ? h->scale : nullptr;
     fa.split = split_table(h, raw);
     fa.debug_out = nullptr;
+    return fa;
+}
+
+int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off) {
+    if (narrow(h) && !h->scales_ready) {
+        int rc = estimate_scales(h, din, S);
+        if (rc != CORR_OK) return rc;
+    }
+    const FengineArgs fa = fengine_args(h, din, S, raw, off);
     const int j = h->f_next;
     cudaStream_t st = h->f_stream[j];
     if (h->prof_on && !h->f_span) {
@@ -1318,6 +1323,7 @@ struct corr_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t graph_frames[kMaxTcModes] = {};
+    bool one_f = false;          // a pass's F-engines as one multi-mode launch
     std::string err = "no error";
 };
 
@@ -1367,14 +1373,23 @@ int batch_enqueue(corr_batch_t b, const uint8_t* const* samples, const int64_t* 
         TcRun runs[kMaxTcModes];
         int idx[kMaxTcModes];
         int na = 0;
+        FengineArgs fas[kMaxTcModes];
         for (int m = 0; m < b->n; ++m) {
             corr_t h = b->h[m];
             const int64_t f0 = pi * h->cap;
             if (f0 >= frames[m]) continue;
             const int64_t S = std::min(h->cap, frames[m] - f0);
             const int64_t rec = (int64_t)h->N * (h->K / 2);
-            int rc = fengine_pass(h, samples[m] + f0 * rec, S, false, 0);
-            if (rc != CORR_OK) return batch_from_handle(b, m, rc);
+            if (b->one_f) {
+                if (narrow(h) && !h->scales_ready) {
+                    int rc = estimate_scales(h, samples[m] + f0 * rec, S);
+                    if (rc != CORR_OK) return batch_from_handle(b, m, rc);
+                }
+                fas[na] = fengine_args(h, samples[m] + f0 * rec, S, false, 0);
+            } else {
+                int rc = fengine_pass(h, samples[m] + f0 * rec, S, false, 0);
+                if (rc != CORR_OK) return batch_from_handle(b, m, rc);
+            }
             TcRun r{};
             r.S_pad = pad_frames(S);
             r.partial = h->partial;
@@ -1386,12 +1401,25 @@ int batch_enqueue(corr_batch_t b, const uint8_t* const* samples, const int64_t* 
             runs[na] = r;
             idx[na++] = m;
         }
-        // the modes' F-engines run side by side; the launch waits for all
-        for (int a = 0; a < na; ++a) {
-            int rc = join_fengines(b->h[idx[a]]);
-            if (rc != CORR_OK) return batch_from_handle(b, idx[a], rc);
-        }
         corr_t h0 = b->h[idx[0]];
+        if (b->one_f) {
+            // every mode's F-engine of this pass in one launch
+            prof_begin(h0);
+            cudaError_t fe = launch_fengine_multi(fas, na, b->stream);
+            if (fe != cudaSuccess) {
+                cudaGetLastError();
+                return batch_err(b, CORR_ECUDA, (std::string("multi-mode F-engine launch: ") +
+                                                 cudaGetErrorString(fe)).c_str());
+            }
+            prof_end(h0, CORR_KERNEL_FENGINE);
+        } else {
+            // the modes' F-engines run side by side; the launch waits for all
+            for (int a = 0; a < na; ++a) {
+                int rc = join_fengines(b->h[idx[a]]);
+                if (rc != CORR_OK) return batch_from_handle(b, idx[a], rc);
+            }
+        }
+        // one tensor-core launch over all of them
         prof_begin(h0);
         int rc = tc_launch(plans, na, runs, b->stream, b->err);
         if (rc != CORR_OK) return rc;
@@ -1456,6 +1484,14 @@ int corr_batch_set_tiles(corr_batch_t b, int window, int stages, int split, int 
         int rc = corr_set_tiles(b->h[m], window, stages, split, atoms);
         if (rc != CORR_OK) return batch_from_handle(b, m, rc);
     }
+    return CORR_OK;
+}
+
+int corr_batch_set_one_launch(corr_batch_t b, int on) {
+    if (!b) return CORR_EINVAL;
+    if (on != 0 && on != 1) return batch_err(b, CORR_EINVAL, "on must be 0 or 1");
+    if (b->one_f != (on == 1)) batch_free_graph(b);   // a recorded step has the other form
+    b->one_f = on == 1;
     return CORR_OK;
 }
 

@@ -103,6 +103,10 @@ struct FengineArgs {
 };
 
 cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st);
+// The F-engines of n modes (1 <= n <= 4, one workspace element type, no
+// debug output) as one launch: each mode's frames as its own kernel would
+// transform them.
+cudaError_t launch_fengine_multi(const FengineArgs* modes, int n, cudaStream_t st);
 
 // Coarse integer delays on the packed stream: out = in delayed by delays[i]
 // samples (0..K) per antenna, S frames [S][N][K/2].  The frame before the

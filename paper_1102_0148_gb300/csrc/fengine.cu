@@ -11,6 +11,7 @@
 // samples: X[k] = E[k] + W_K^k O[k], E[k] = (Z[k] + conj Z[L-k]) / 2,
 // O[k] = (Z[k] - conj Z[L-k]) / 2i, L = K/2.
 #include "corr_internal.h"
+#include "xengine_tc.h"
 #include "fengine_k512.cuh"
 
 #include <cuda_fp8.h>
@@ -61,17 +62,16 @@ __device__ __forceinline__ float2 real_split(const float2* Z, int k, int L, cons
 // antenna, one frame at a time, with a radix-2 Stockham FFT in shared memory;
 // the FT results of each channel are staged and written as one contiguous run
 // of the workspace row (k, r).
-template <bool DEBUG>
-__global__ void __launch_bounds__(kThreads) fengine_generic(FengineArgs a, int FT) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+// The body: FT frames from s0 of antenna i by kThreads threads (tid), `smem`
+// 16 L + (DEBUG ? 0 : 8 C FT) bytes, `sync` a barrier of those threads.
+template <bool DEBUG, class Sync>
+__device__ __forceinline__ void fgeneric_block(const FengineArgs& a, int FT, int i, int64_t s0,
+                                               unsigned char* smem, int tid, Sync sync) {
     const int L = a.K >> 1;
     const int C = L;
-    float2* bufA = reinterpret_cast<float2*>(smem_raw);
+    float2* bufA = reinterpret_cast<float2*>(smem);
     float2* bufB = bufA + L;
     float* stg = reinterpret_cast<float*>(bufB + L);       // [2][C][FT]
-    const int i = blockIdx.y;
-    const int64_t s0 = (int64_t)blockIdx.x * FT;
-    const int tid = threadIdx.x;
     const int64_t s_end = DEBUG ? a.S : a.S_pad;
 
     for (int f = 0; f < FT; ++f) {
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kThreads) fengine_generic(FengineArgs a, int F
             }
             bufA[m] = z;
         }
-        __syncthreads();
+        sync();
         float2* x = bufA;
         float2* y = bufB;
         for (int Ns = 1; Ns < L; Ns <<= 1) {
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kThreads) fengine_generic(FengineArgs a, int F
                 y[d] = make_float2(v0.x + v1.x, v0.y + v1.y);
                 y[d + Ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
             }
-            __syncthreads();
+            sync();
             float2* t = x;
             x = y;
             y = t;
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kThreads) fengine_generic(FengineArgs a, int F
                 stg[(C + k) * FT + f] = X.y;
             }
         }
-        __syncthreads();
+        sync();
     }
     if (!DEBUG) {
         const float sigma = a.spec_type == SPEC_F16X2 ? __ldg(a.split + i) : 1.0f;
@@ -136,6 +136,13 @@ __global__ void __launch_bounds__(kThreads) fengine_generic(FengineArgs a, int F
             store_spec(a.spec, a.spec_type, off, stg[row * FT + f], a.plane_stride, sigma);
         }
     }
+}
+
+template <bool DEBUG>
+__global__ void __launch_bounds__(kThreads) fengine_generic(FengineArgs a, int FT) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fgeneric_block<DEBUG>(a, FT, blockIdx.y, (int64_t)blockIdx.x * FT, smem_raw, threadIdx.x,
+                          []() { __syncthreads(); });
 }
 
 // K = 512 kernel: one 32-frame block of one antenna per CTA (the body is
@@ -199,23 +206,22 @@ constexpr int kStg1024Row = 1058;
 constexpr int kStg1024Floats = kF1024Frames * kStg1024Row;
 static_assert(kStg1024Row % 8 == 2 && kStg1024Row >= 16 * kX1024Stride * 2 + 2, "staging row layout");
 
-template <int OUT, bool CORR>
-__global__ void __launch_bounds__(kF1024Threads, 3) fengine_k1024(FengineArgs a) {
+// The body: 16 frames from s0 of antenna i by kF1024Threads threads (tid),
+// `smem` as the kernel's dynamic shared memory, `sync` a barrier of them.
+template <int OUT, bool CORR, class Sync>
+__device__ __forceinline__ void f1024_block(const FengineArgs& a, int i, int64_t s0,
+                                            unsigned char* smem, int tid, Sync sync) {
     constexpr bool DEBUG = OUT == kOutDebug;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* stg = reinterpret_cast<float*>(smem_raw);                        // [16][1058]
+    float* stg = reinterpret_cast<float*>(smem);                            // [16][1058]
     float2* tw_base = reinterpret_cast<float2*>(stg + kStg1024Floats);      // [2][4 m][32 t]
     float2* tw32 = tw_base + 256;                                           // [2][16]
     constexpr bool kScaled = OUT == SPEC_F16 || OUT == SPEC_F8;
     float* sc_tab = reinterpret_cast<float*>(tw32 + 32);                    // [512] if kScaled
 
-    const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const int k1 = lane & 15;
     const int hh = lane >> 4;
-    const int i = a.ant_x ? blockIdx.x : blockIdx.y;
-    const int64_t s0 = (int64_t)(a.ant_x ? blockIdx.y : blockIdx.x) * kF1024Frames;
     const float post = OUT == SPEC_F16X2 ? __ldg(a.split + i) : 1.0f;
     const float chalf = 0.5f * post;
     // Twiddles as in the K = 512 kernel: the stage twiddle W512^{t q},
@@ -239,7 +245,7 @@ __global__ void __launch_bounds__(kF1024Threads, 3) fengine_k1024(FengineArgs a)
         if (sa < a.S) raw0 = __ldg(reinterpret_cast<const uint4*>(a.in + (sa * a.N + i) * 512) + lane);
         if (sb < a.S) raw1 = __ldg(reinterpret_cast<const uint4*>(a.in + (sb * a.N + i) * 512) + lane);
     }
-    __syncthreads();
+    sync();
 
     const int fx = warp + 8;                         // the warp's second frame
     float2* gx = reinterpret_cast<float2*>(stg + fx * kStg1024Row + 2 * (fx & 1));
@@ -336,7 +342,7 @@ __global__ void __launch_bounds__(kF1024Threads, 3) fengine_k1024(FengineArgs a)
         }
     }
     if (DEBUG) return;
-    __syncthreads();
+    sync();
     // 1024 workspace rows (plane, k) x 16 frames: 4 lanes per row, 4 frames each
     const int m = lane & 3;
     for (int row = 8 * warp + (lane >> 2); row < 1024; row += 8 * (kF1024Threads / 32)) {
@@ -348,6 +354,14 @@ __global__ void __launch_bounds__(kF1024Threads, 3) fengine_k1024(FengineArgs a)
         store4<OUT>(a.spec, off, a.plane_stride, src[0], src[kStg1024Row], src[2 * kStg1024Row],
                     src[3 * kStg1024Row]);
     }
+}
+
+template <int OUT, bool CORR>
+__global__ void __launch_bounds__(kF1024Threads, 3) fengine_k1024(FengineArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int i = a.ant_x ? blockIdx.x : blockIdx.y;
+    const int64_t s0 = (int64_t)(a.ant_x ? blockIdx.y : blockIdx.x) * kF1024Frames;
+    f1024_block<OUT, CORR>(a, i, s0, smem_raw, threadIdx.x, []() { __syncthreads(); });
 }
 
 // ---------------------------------------------------------------------------
@@ -421,23 +435,23 @@ struct Rad16Shape {
     }
 };
 
-template <int R, int OUT>
-__global__ void __launch_bounds__(kRadThreads, 1) fengine_rad16(FengineArgs a) {
+// The body: FT frames from s0 of antenna i by kRadThreads threads (tid),
+// `smem` as the kernel's dynamic shared memory; `sync` is a barrier of the
+// kRadThreads threads and group g syncs on named barrier bar0 + g.
+template <int R, int OUT, class Sync>
+__device__ __forceinline__ void frad16_block(const FengineArgs& a, int i, int64_t s0,
+                                             unsigned char* smem, int tid, int bar0, Sync sync) {
     constexpr bool DEBUG = OUT == kOutDebug;
     using Sh = Rad16Shape<R>;
-    constexpr int L = Sh::L, B = Sh::B, Q = Sh::Q, G = Sh::G, FT = Sh::FT, M = Sh::M,
-                  SR = Sh::SR, XB = Sh::XB;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* stg = reinterpret_cast<float*>(smem_raw);                            // [FT][SR]
+    constexpr int L = Sh::L, B = Sh::B, Q = Sh::Q, G = Sh::G, M = Sh::M, SR = Sh::SR,
+                  XB = Sh::XB;
+    float* stg = reinterpret_cast<float*>(smem);                                // [FT][SR]
     float2* xbuf = reinterpret_cast<float2*>(stg + (DEBUG ? 0 : Sh::STG));      // [G][XB]
     float2* tw1 = xbuf + G * XB;                                                // [16 k1][B t]
     float2* tw2 = tw1 + 16 * B;                                                 // [R r][16 k2]
 
-    const int tid = threadIdx.x;
     const int g = tid / B;
     const int t = tid - g * B;
-    const int i = blockIdx.y;
-    const int64_t s0 = (int64_t)blockIdx.x * FT;
     const float post = OUT == SPEC_F16X2 ? __ldg(a.split + i) : 1.0f;
     const float chalf = 0.5f * post;
 
@@ -454,11 +468,11 @@ __global__ void __launch_bounds__(kRadThreads, 1) fengine_rad16(FengineArgs a) {
         if (sa < a.S) raw0 = __ldg(reinterpret_cast<const uint4*>(a.in + (sa * a.N + i) * L) + t);
         if (sb < a.S) raw1 = __ldg(reinterpret_cast<const uint4*>(a.in + (sb * a.N + i) * L) + t);
     }
-    __syncthreads();
+    sync();
 
     float2* xb = xbuf + g * XB;
     const unsigned char* xbytes = reinterpret_cast<const unsigned char*>(xb);
-    const int bar = 1 + g;
+    const int bar = bar0 + g;
     const int k1 = t & 15, r = t >> 4;
 
 #pragma unroll 1
@@ -531,7 +545,7 @@ __global__ void __launch_bounds__(kRadThreads, 1) fengine_rad16(FengineArgs a) {
         group_bar(bar, B);
     }
     if (DEBUG) return;
-    __syncthreads();
+    sync();
     // 2L workspace rows (plane, k) x FT frames: M lanes per row, 4 frames each
     const int l32 = tid & 31, warp = tid >> 5;
     const int m = l32 % M;
@@ -544,6 +558,126 @@ __global__ void __launch_bounds__(kRadThreads, 1) fengine_rad16(FengineArgs a) {
         const int64_t off = spec_off(k, spec_row(plane, i, a.N), a.s_base + s0 + 4 * m, a.N,
                                      a.K >> 1, spec_tile_shift(OUT));
         store4<OUT>(a.spec, off, a.plane_stride, src[0], src[SR], src[2 * SR], src[3 * SR]);
+    }
+}
+
+template <int R, int OUT>
+__global__ void __launch_bounds__(kRadThreads, 1) fengine_rad16(FengineArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    frad16_block<R, OUT>(a, blockIdx.y, (int64_t)blockIdx.x * Rad16Shape<R>::FT, smem_raw,
+                         threadIdx.x, 1, []() { __syncthreads(); });
+}
+
+// ---------------------------------------------------------------------------
+// Several modes' F-engines in one launch (the batching form): one persistent
+// CTA of 768 threads per SM.  First every K = 2048 / 4096 block, each by the
+// CTA's first 512 threads with the body of its standalone kernel (barriers
+// 1 and 2 ..); after a CTA-wide barrier the three 256-thread sub-blocks each
+// walk their own share of the K = 512, 1024 and generic-K blocks, with their
+// own shared memory and named barrier (1 + sub-block).  The sub-blocks drift
+// apart, so one's loads and FFT overlap another's stores as three separate
+// CTAs of the standalone kernels do.  (Non-persistent CTAs of three
+// sub-blocks started and ended their phases together: 20-30% slower.)
+// ---------------------------------------------------------------------------
+
+enum FKind { kFK512 = 0, kFK1024 = 1, kFKRad4 = 2, kFKRad8 = 3, kFKGeneric = 4 };
+constexpr int kMultiThreads = 768;
+constexpr int kMultiSubs = kMultiThreads / 256;
+
+struct FModeDesc {
+    FengineArgs a;
+    int kind;
+    int FT;              // frames per block of the body
+    int64_t nblk;        // blocks: antennas x frame blocks (antenna fastest)
+    int64_t blk0;        // first block of the mode in its phase's numbering
+    uint32_t sub_bytes;  // shared memory of one 256-thread sub-block, or of the body
+};
+
+struct FMultiArgs {
+    FModeDesc md[kMaxTcModes];
+    int n;
+    int64_t rad_blocks;  // phase 1: blocks of the K = 2048 / 4096 modes
+    int64_t sub_blocks;  // phase 2: blocks of the other modes
+    uint32_t sub_stride; // phase 2: shared memory per sub-block (the largest mode's),
+                         // so sub-blocks on different modes never overlap
+};
+
+__device__ __forceinline__ bool fk_rad(int kind) { return kind == kFKRad4 || kind == kFKRad8; }
+
+// Named-barrier sync of `n` threads.
+struct BarSync {
+    int id, n;
+    __device__ void operator()() const { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+};
+
+template <int OUT>
+__global__ void __launch_bounds__(kMultiThreads, 1) fengine_multi(const __grid_constant__ FMultiArgs m) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x;
+    if (tid < kRadThreads) {
+        const BarSync sync{1, kRadThreads};
+        for (int64_t g = blockIdx.x; g < m.rad_blocks; g += gridDim.x) {
+            int mi = 0;
+            while (!fk_rad(m.md[mi].kind) || g >= m.md[mi].blk0 + m.md[mi].nblk) ++mi;
+            const FModeDesc& d = m.md[mi];
+            const FengineArgs& a = d.a;
+            const int64_t vb = g - d.blk0;
+            const int i = (int)(vb % a.N);
+            const int64_t s0 = (vb / a.N) * d.FT;
+            if (d.kind == kFKRad4)
+                frad16_block<4, OUT>(a, i, s0, smem_raw, tid, 2, sync);
+            else
+                frad16_block<8, OUT>(a, i, s0, smem_raw, tid, 2, sync);
+            sync();                      // the staging is the next block's
+        }
+    }
+    if (m.rad_blocks > 0) asm volatile("bar.sync 15, 768;" ::: "memory");
+    const int sub = tid >> 8;
+    const int t = tid & 255;
+    const BarSync sync{1 + sub, 256};
+    for (int64_t g = (int64_t)blockIdx.x * kMultiSubs + sub; g < m.sub_blocks;
+         g += (int64_t)gridDim.x * kMultiSubs) {
+        int mi = 0;
+        while (fk_rad(m.md[mi].kind) || g >= m.md[mi].blk0 + m.md[mi].nblk) ++mi;
+        const FModeDesc& d = m.md[mi];
+        const FengineArgs& a = d.a;
+        const int64_t vb = g - d.blk0;
+        const int i = (int)(vb % a.N);
+        const int64_t s0 = (vb / a.N) * d.FT;
+        unsigned char* sm = smem_raw + (size_t)sub * m.sub_stride;
+        if (d.kind == kFK512) {
+            constexpr bool kScaled = OUT == SPEC_F16 || OUT == SPEC_F8;
+            float* stg = reinterpret_cast<float*>(sm);
+            float2* tw_base = reinterpret_cast<float2*>(stg + kStgFloats);
+            float* sc_tab = reinterpret_cast<float*>(tw_base + 128);
+            float2* corr_tab = reinterpret_cast<float2*>(sc_tab + (kScaled ? 256 : 0));
+            F512Block b;
+            b.in = a.in + (s0 * a.N + i) * 256;
+            b.stride = (int64_t)a.N * 256;
+            b.nvalid = (int)max((int64_t)0, min((int64_t)kF512Frames, a.S - s0));
+            b.ant = i;
+            b.post = OUT == SPEC_F16X2 ? __ldg(a.split + i) : 1.0f;
+            b.spec = static_cast<char*>(a.spec);
+            b.s = a.s_base + s0;
+            b.N = a.N;
+            b.plane_stride = a.plane_stride;
+            b.debug = nullptr;
+            const float* sc = kScaled ? a.scale + (int64_t)i * 256 : nullptr;
+            if (a.corr)
+                f512_block<OUT, true>(b, a.twiddle, a.corr + (int64_t)i * 256, sc, stg, tw_base,
+                                      sc_tab, corr_tab, t, sync);
+            else
+                f512_block<OUT, false>(b, a.twiddle, nullptr, sc, stg, tw_base, sc_tab, corr_tab, t,
+                                       sync);
+        } else if (d.kind == kFK1024) {
+            if (a.corr)
+                f1024_block<OUT, true>(a, i, s0, sm, t, sync);
+            else
+                f1024_block<OUT, false>(a, i, s0, sm, t, sync);
+        } else {
+            fgeneric_block<false>(a, d.FT, i, s0, sm, t, sync);
+        }
+        sync();                          // the staging is the next block's
     }
 }
 
@@ -682,6 +816,77 @@ cudaError_t launch_fengine(const FengineArgs& a, cudaStream_t st) {
         fengine_generic<false><<<grid, kThreads, smem, st>>>(a, FT);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_fengine_multi(const FengineArgs* modes, int n, cudaStream_t st) {
+    if (n < 1 || n > kMaxTcModes) return cudaErrorInvalidValue;
+    FMultiArgs m{};
+    size_t smem = 0;
+    const int out = modes[0].spec_type;
+    for (int q = 0; q < n; ++q) {
+        const FengineArgs& a = modes[q];
+        if (a.debug_out || a.spec_type != out) return cudaErrorInvalidValue;
+        if (a.S_pad <= 0) continue;
+        FModeDesc& d = m.md[m.n];
+        d.a = a;
+        const bool al16 = (reinterpret_cast<uintptr_t>(a.in) & 15) == 0;
+        const bool scaled = out == SPEC_F16 || out == SPEC_F8;
+        size_t bytes;
+        if (a.K == 512 && al16) {
+            d.kind = kFK512;
+            d.FT = kF512Frames;
+            bytes = (size_t)kStgFloats * sizeof(float) + 128 * sizeof(float2) +
+                    (scaled ? 256 * sizeof(float) : 0) + (a.corr ? 256 * sizeof(float2) : 0);
+        } else if (a.K == 1024 && al16) {
+            d.kind = kFK1024;
+            d.FT = kF1024Frames;
+            bytes = (size_t)kStg1024Floats * sizeof(float) + (256 + 32) * sizeof(float2) +
+                    (scaled ? 512 * sizeof(float) : 0);
+        } else if (a.K == 2048 && al16) {
+            d.kind = kFKRad4;
+            d.FT = Rad16Shape<4>::FT;
+            bytes = Rad16Shape<4>::smem(false);
+        } else if (a.K == 4096 && al16) {
+            d.kind = kFKRad8;
+            d.FT = Rad16Shape<8>::FT;
+            bytes = Rad16Shape<8>::smem(false);
+        } else {
+            d.kind = kFKGeneric;
+            const int C = a.K / 2;
+            d.FT = std::max(1, std::min(32, 8192 / C));
+            bytes = (size_t)16 * (a.K / 2) + (size_t)8 * C * d.FT;
+        }
+        bytes = (bytes + 127) & ~(size_t)127;
+        const bool rad = d.kind == kFKRad4 || d.kind == kFKRad8;
+        d.sub_bytes = (uint32_t)bytes;
+        d.nblk = (int64_t)a.N * ((a.S_pad + d.FT - 1) / d.FT);
+        int64_t& count = rad ? m.rad_blocks : m.sub_blocks;
+        d.blk0 = count;
+        count += d.nblk;
+        if (!rad) m.sub_stride = std::max<uint32_t>(m.sub_stride, (uint32_t)bytes);
+        smem = std::max(smem, rad ? bytes : bytes * kMultiSubs);
+        ++m.n;
+    }
+    if (m.n == 0) return cudaSuccess;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t need = std::max(m.rad_blocks, (m.sub_blocks + kMultiSubs - 1) / kMultiSubs);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nsm, need));
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (r != cudaSuccess) return r;
+        kern<<<grid, kMultiThreads, smem, st>>>(m);
+        return cudaGetLastError();
+    };
+    switch (out) {
+        case SPEC_F32: return go(fengine_multi<SPEC_F32>);
+        case SPEC_F16: return go(fengine_multi<SPEC_F16>);
+        case SPEC_F8: return go(fengine_multi<SPEC_F8>);
+        default: return go(fengine_multi<SPEC_F16X2>);
+    }
 }
 
 // ---------------------------------------------------------------------------

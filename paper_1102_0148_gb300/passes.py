@@ -57,7 +57,7 @@ def run(N, K, dtype="fp32", frames=4096, steps=5, warmup=3, window=0, stages=0, 
 
 
 def run_batch(modes, dtype="fp16", samples=1 << 22, steps=20, warmup=3, window=0, stages=0,
-              split=0, seed=5):
+              split=0, seed=5, one_launch=False):
     """Replays of the captured step of a batch (push of ``samples`` per antenna
     and mode, one pass per mode, and the dump), timed with CUDA events on the
     batch's stream; eager per-class launch counts of one step."""
@@ -66,18 +66,25 @@ def run_batch(modes, dtype="fp16", samples=1 << 22, steps=20, warmup=3, window=0
     for m, (N, K) in enumerate(modes):
         d, _ = synth.make_samples_torch(N, samples, K, seed=seed + m, device="cuda")
         data.append(d.reshape(-1))
-    with corr.CorrelatorBatch(modes, dtype, window=window, stages=stages, split=split) as b:
+    with corr.CorrelatorBatch(modes, dtype, window=window, stages=stages, split=split,
+                              one_launch=one_launch) as b:
         for h, (N, K) in zip(b.handles, modes):
             corr.corr_set_chunk(h, samples // K)
             corr.corr_profile_enable(h, True)
             corr.corr_profile_read(h)
         b.push(data)
         b.dump()
-        launches = {}
+        b.push(data)                     # the second eager step is the one profiled
         for h in b.handles:
-            for c, (n, _) in corr.corr_profile_read(h).items():
+            corr.corr_profile_read(h)
+        b.push(data)
+        b.dump()
+        launches, eager_ms = {}, {}
+        for h in b.handles:
+            for c, (n, t) in corr.corr_profile_read(h).items():
                 if n:
                     launches[c] = launches.get(c, 0) + n
+                    eager_ms[c] = eager_ms.get(c, 0.0) + t
             corr.corr_profile_enable(h, False)
         vis = [torch.empty((N * (N + 1) // 2, K // 2), dtype=torch.complex64, device="cuda")
                for N, K in modes]
@@ -95,7 +102,7 @@ def run_batch(modes, dtype="fp16", samples=1 << 22, steps=20, warmup=3, window=0
         b.sync()
         ms = e0.elapsed_time(e1) / steps
     return {"modes": [list(m) for m in modes], "dtype": dtype, "samples": samples,
-            "ms_per_step": ms, "launches_per_step": launches}
+            "one_launch": one_launch, "ms_per_step": ms, "launches_per_step": launches, "eager_ms_per_class": eager_ms}
 
 
 def main():
@@ -105,6 +112,8 @@ def main():
     ap.add_argument("--batch", default=None,
                     help="modes N:K,N:K,... (a captured batch step instead of one handle)")
     ap.add_argument("--samples", type=int, default=1 << 22, help="per antenna and mode (--batch)")
+    ap.add_argument("--one-launch", action="store_true",
+                    help="(--batch) the modes' F-engines as one launch")
     ap.add_argument("--dtype", default="fp32", choices=sorted(corr.DTYPES))
     ap.add_argument("--frames", type=int, default=4096)
     ap.add_argument("--steps", type=int, default=5)
@@ -117,7 +126,7 @@ def main():
     if a.batch:
         modes = [tuple(int(v) for v in m.split(":")) for m in a.batch.split(",")]
         print(json.dumps(run_batch(modes, a.dtype, a.samples, a.steps, a.warmup, a.window,
-                                   a.stages, a.split)))
+                                   a.stages, a.split, one_launch=a.one_launch)))
         return
     if a.N is None or a.K is None:
         ap.error("--N and --K (or --batch) are required")

@@ -38,10 +38,12 @@ def make_inputs(modes, T, seed):
     return packed, refs
 
 
+# one: the modes' F-engines as one multi-mode launch (corr_batch_set_one_launch)
+@pytest.mark.parametrize("one", [False, True])
 @pytest.mark.parametrize("modes,T", [(MODES3, 1 << 17), (MODES4, 1 << 16)])
-def test_batch_matches_oracle(lib, modes, T):
+def test_batch_matches_oracle(lib, modes, T, one):
     dev, refs = make_inputs(modes, T, seed=11020148 + 40)
-    with lib.CorrelatorBatch(modes, "fp32") as b:
+    with lib.CorrelatorBatch(modes, "fp32", one_launch=one) as b:
         b.push(dev)
         vis, n = b.dump(fp64=True)
     for (N, K), V, R, nm in zip(modes, vis, refs, n):
@@ -64,14 +66,15 @@ def test_batch_multiple_passes(lib):
         assert norm_err(V, 2 * R, N) <= 1e-5
 
 
-def test_batch_graph_replay(lib):
+@pytest.mark.parametrize("one", [False, True])
+def test_batch_graph_replay(lib, one):
     import torch
     modes = MODES3
     T = 1 << 16
     dev_a, refs_a = make_inputs(modes, T, seed=11020148 + 42)
     dev_b, refs_b = make_inputs(modes, T, seed=11020148 + 43)
     bufs = [x.clone() for x in dev_a]
-    with lib.CorrelatorBatch(modes, "fp32") as b:
+    with lib.CorrelatorBatch(modes, "fp32", one_launch=one) as b:
         vis = [torch.empty((N * (N + 1) // 2, K // 2), dtype=torch.complex128, device="cuda")
                for N, K in modes]
         b.capture(bufs, vis, fp64=True)
@@ -86,11 +89,12 @@ def test_batch_graph_replay(lib):
                 assert norm_err(V.cpu().numpy(), R, N) <= 1e-5
 
 
-def test_batch_fp16(lib):
+@pytest.mark.parametrize("one", [False, True])
+def test_batch_fp16(lib, one):
     modes = MODES3
     T = 1 << 17
     dev, refs = make_inputs(modes, T, seed=11020148 + 44)
-    with lib.CorrelatorBatch(modes, "fp16") as b:
+    with lib.CorrelatorBatch(modes, "fp16", one_launch=one) as b:
         b.push(dev)
         vis, n = b.dump(fp64=True)
     for (N, K), V, R in zip(modes, vis, refs):
@@ -107,7 +111,8 @@ def test_batch_rejects_mixed_or_bad_arguments(lib):
         lib.CorrelatorBatch(MODES3, "fp32_simt")
 
 
-def test_batch_multiblock_passes_and_replays(lib):
+@pytest.mark.parametrize("one", [False, True])
+def test_batch_multiblock_passes_and_replays(lib, one):
     """A multi-block mode (N = 130: three antenna blocks) whose pass results
     go through the FP32 slot and the reduction: several passes per push (the
     first into a zero accumulator is stored, later ones added), pushes
@@ -118,7 +123,7 @@ def test_batch_multiblock_passes_and_replays(lib):
     T = 1 << 16                                   # 256 and 128 frames
     dev_a, refs_a = make_inputs(modes, T, seed=11020148 + 45)
     dev_b, refs_b = make_inputs(modes, T, seed=11020148 + 46)
-    with lib.CorrelatorBatch(modes, "fp32", chunk=128) as b:   # 2 passes and 1 per push
+    with lib.CorrelatorBatch(modes, "fp32", chunk=128, one_launch=one) as b:   # 2 passes and 1
         b.push(dev_a)
         b.push(dev_b)
         vis, n = b.dump(fp64=True)
@@ -144,3 +149,29 @@ def test_batch_multiblock_passes_and_replays(lib):
         vis, n = b.dump(fp64=True)                # the eager push is still whole
         for (N, K), V, R in zip(modes, vis, refs_a):
             assert norm_err(V, R, N) <= 1e-5, (N, K)
+
+
+@pytest.mark.parametrize("one", [False, True])
+def test_batch_every_fengine_kind_with_corrections(lib, one):
+    """Every F-engine body -- K = 512, 1024, 2048 and a generic K (256) --
+    each mode with its own gains and fractional delays, as separate launches
+    and as one multi-mode launch, against the oracle with the same
+    corrections."""
+    modes = [(44, 512), (20, 1024), (22, 2048), (5, 256)]
+    T = 1 << 16
+    dev, _ = make_inputs(modes, T, seed=11020148 + 47)
+    refs = []
+    with lib.CorrelatorBatch(modes, "fp32", one_launch=one) as b:
+        for m, ((N, K), h) in enumerate(zip(modes, b.handles)):
+            g, tau = synth.gains_delays(N, seed=500 + m)
+            g32 = np.asarray(g, np.complex64)
+            t32 = np.asarray(tau * 2.5, np.float32)
+            lib.corr_set_corrections(h, g32, t32)
+            packed = dev[m].cpu().numpy().reshape(T // K, N, K // 2)
+            refs.append(oracle.correlate(packed, N, K, gains=g32.astype(np.complex128),
+                                         delays=t32.astype(np.float64))[0])
+        b.push(dev)
+        vis, n = b.dump(fp64=True)
+    for (N, K), V, R, nm in zip(modes, vis, refs, n):
+        assert nm == T // K
+        assert norm_err(V, R, N) <= 1e-5, (N, K)

@@ -272,6 +272,38 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" :::
 
 // --------------------------------------------------------------------- kernel
 
+// Stage layout of one item.  A group (several antenna blocks) fills each
+// k-tile's atom of the launch's layout.  A single-block item packs its tiles
+// densely: atom = [hi | lo] tiles of its own box (2N rows rounded up to 8),
+// as many per stage as fit and divide a window, so a single-block mode in a
+// launch with a multi-block one still moves up to a window of spectra per
+// stage handshake.  (In a launch of single-block modes only this is the
+// launch's own layout for the largest mode and denser for smaller ones.)
+struct ItemLayout {
+    uint32_t atom;      // bytes per k-tile
+    uint32_t plo;       // hi -> lo plane within a k-tile
+    int at;             // k-tiles per stage
+};
+
+__device__ __forceinline__ ItemLayout item_layout(const TcArgs& a, const TcModeArgs& d, bool single,
+                                                  int planes, uint32_t stage_bytes,
+                                                  uint32_t atom_bytes, uint32_t plane_off) {
+    ItemLayout L;
+    if (!single) {
+        L.atom = atom_bytes;
+        L.plo = plane_off;
+        L.at = a.atoms;
+        return L;
+    }
+    L.atom = (uint32_t)planes * d.box_bytes;
+    L.plo = d.box_bytes;
+    const int wk = a.W >> a.kt_shift;                 // k-tiles per window
+    int at = (int)min((uint32_t)wk, stage_bytes / L.atom);
+    while (at > 1 && wk % at) --at;
+    L.at = max(at, 1);
+    return L;
+}
+
 // WIDE: some mode of the launch has several antenna blocks (work groups of
 // one A block and two B blocks); launches of single-block modes only take
 // the narrow instance, which has none of the group code.
@@ -281,15 +313,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     constexpr int planes = MODE == 0 ? 2 : 1;
-    // Stage layout: per k-tile ("atom") the A slot of each plane [hi | lo];
-    // when a mode of the launch has several antenna blocks (WIDE), then the
-    // B slots [B0 hi | B1 hi | B0 lo | B1 lo] (one plane: [B0 | B1]), so a
-    // group's two B blocks form one operand of 256 rows.  A slot has
-    // slot_rows rows (2N rounded up to 8 for one antenna block, else 128).
-    // The MMA reads 128 rows (and a single-block pair's concatenated B operand
-    // 2 slot_rows rows) from a slot; rows past the antennas only feed outputs
-    // the epilogue ignores, and the ring is followed by enough shared memory
-    // for the reads past its last slot.
+    // Stage layout of a group (several antenna blocks, WIDE): per k-tile
+    // ("atom") the A slot of each plane [hi | lo], then the B slots
+    // [B0 hi | B1 hi | B0 lo | B1 lo] (one plane: [B0 | B1]), so a group's
+    // two B blocks form one operand of 256 rows; a slot has slot_rows = 128
+    // rows.  A single-block item packs its k-tiles densely instead
+    // ([hi | lo] of its own 2N-rounded-up-to-8 rows each, item_layout).  The
+    // MMA reads 128 rows from a tile (and a single block's concatenated
+    // [hi; lo] B operand 2 box rows); rows past the antennas only feed
+    // outputs the epilogue ignores, and the ring is followed by enough shared
+    // memory for the reads past its last tile.
     const uint32_t slot = (uint32_t)a.slot_rows * (uint32_t)a.row_bytes;
     constexpr int KK = MODE == 2 ? 4 : 2;       // MMA k-steps (32 bytes of a row) per k-tile
     const uint32_t plane_off = slot;                                // A: hi -> lo plane
@@ -297,7 +330,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
     const uint32_t bl_off = bh_off + 2 * slot;                      // B0 lo (planes == 2)
     const uint32_t atom_bytes = planes * slot * (WIDE ? 3u : 1u);
     const uint32_t stage_bytes = atom_bytes * (uint32_t)a.atoms;
-    const int step = a.KT * a.atoms;                             // spectra per stage
     unsigned char* stages = smem;
     float* Gs = reinterpret_cast<float*>(smem + a.stages * stage_bytes);   // <= 128 x 129
     // WIDE: each epilogue warp's staging rows for V, [16][kVRow] float2
@@ -365,9 +397,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                 const int ra = kRows * itm.b1;
                 const int rb = kRows * itm.b2;
                 const uint32_t ntile = single ? 1u : (uint32_t)itm.nbB + (alias ? 0u : 1u);
+                const ItemLayout lay = item_layout(a, d, single, planes, stage_bytes, atom_bytes, plane_off);
+                const int step_i = a.KT * lay.at;
                 const int64_t s_beg = pc.s_beg;
                 const int64_t s_end = pc.s_end;
-                for (int64_t s = s_beg; s < s_end; s += step, ++it) {
+                for (int64_t s = s_beg; s < s_end; s += step_i, ++it) {
                     if (it > 0 && ++st == (uint32_t)a.stages) {
                         st = 0;
                         ph ^= 1u;
@@ -377,18 +411,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                         break;
                     }
                     if (a.withhold && blockIdx.x == 0 && it == 0) continue;   // test hook
-                    const int n_at = (int)min((int64_t)a.atoms, (s_end - s) >> a.kt_shift);
+                    const int n_at = (int)min((int64_t)lay.at, (s_end - s) >> a.kt_shift);
                     const uint32_t bytes = (uint32_t)n_at * planes * d.box_bytes * ntile;
                     const uint32_t fb = smem_u32(&full[st]);
                     mbar_expect_tx(fb, bytes);
                     const uint32_t dst = smem_u32(stages + st * stage_bytes);
                     for (int at = 0; at < n_at; ++at) {
                         const int st4 = (int)(s >> a.kt_shift) + at;   // k-tile of the pass
-                        const uint32_t o = (uint32_t)at * atom_bytes;
+                        const uint32_t o = (uint32_t)at * lay.atom;
                         if (!alias) {
                             tma_load_4d(dst + o, map, fb, ra, itm.k, st4);
                             if (planes == 2)
-                                tma_load_4d(dst + plane_off + o, map, fb, ra, itm.k, d.cap_tiles + st4);
+                                tma_load_4d(dst + lay.plo + o, map, fb, ra, itm.k, d.cap_tiles + st4);
                         }
                         if (!single)
                             for (int bb = 0; bb < itm.nbB; ++bb) {
@@ -437,9 +471,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                 // group: A from its own slots, or the first B block's
                 const uint32_t a_hi = alias ? bh_off : 0u;
                 const uint32_t a_lo = alias ? bl_off : plane_off;
-                // FP32 mode, diagonal pair: B = [hi; lo] rows of the same tile pair,
-                // N = 2 slot_rows, so one MMA forms [Dhh | Dhl] (Dhl from column slot_rows)
-                const uint32_t idesc_cat = (1u << 4) | ((uint32_t)((2 * a.slot_rows) >> 3) << 17) |
+                const ItemLayout lay = item_layout(a, d, single, planes, stage_bytes, atom_bytes, plane_off);
+                const int step_i = a.KT * lay.at;
+                // FP32 mode, single block: B = [hi; lo], the k-tile's two tiles
+                // of box_rows rows each, N = 2 box_rows, so one MMA forms
+                // [Dhh | Dhl] (Dhl from column box_rows)
+                const int box_rows = (int)(d.box_bytes / (uint32_t)a.row_bytes);
+                const uint32_t idesc_cat = (1u << 4) | ((uint32_t)((2 * box_rows) >> 3) << 17) |
                                            ((uint32_t)(kRows >> 4) << 24);
                 const int64_t s_beg = pc.s_beg;
                 const int64_t s_end = pc.s_end;
@@ -454,7 +492,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                     const uint32_t d0 = tmem + (uint32_t)b * 256u;
                     const int64_t w1 = min(s_end, w0 + a.W);
                     uint32_t acc = 0;
-                    for (int64_t s = w0; s < w1; s += step, ++it) {
+                    for (int64_t s = w0; s < w1; s += step_i, ++it) {
                         if (it > 0 && ++st == (uint32_t)a.stages) {
                             st = 0;
                             ph ^= 1u;
@@ -465,9 +503,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                         }
                         tc_fence_after();
                         const uint32_t base = smem_u32(stages + st * stage_bytes);
-                        const int n_at = (int)min((int64_t)a.atoms, (w1 - s) >> a.kt_shift);
+                        const int n_at = (int)min((int64_t)lay.at, (w1 - s) >> a.kt_shift);
                         for (int at = 0; at < n_at; ++at) {
-                            const uint32_t ab = base + (uint32_t)at * atom_bytes;
+                            const uint32_t ab = base + (uint32_t)at * lay.atom;
 #pragma unroll
                             for (int kk = 0; kk < KK; ++kk) {
                                 if (single) {
@@ -566,7 +604,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) xengine_tc_kernel(const __grid_
                         tmem_ld8(trow + 8u * c, v);
                         if (c < 8 && use_t) {
                             uint32_t w[8];
-                            tmem_ld8(trow + (uint32_t)a.slot_rows + 8u * c, w);
+                            tmem_ld8(trow + d.box_bytes / (uint32_t)a.row_bytes + 8u * c, w);
                             tmem_ld_wait();
 #pragma unroll
                             for (int j = 0; j < 8; ++j) {
@@ -970,12 +1008,16 @@ LaunchShape launch_shape(TcPlan* const* plans, int n) {
     }
     L.gs_floats = r2max * (r2max + 1);
     L.slot_rows = 8;
-    for (int m = 0; m < n; ++m) L.slot_rows = std::max(L.slot_rows, plans[m]->box_rows);
+    int min_box = kRows;      // the MMA reads 128 rows from a tile: reserve the excess past the ring
+    for (int m = 0; m < n; ++m) {
+        L.slot_rows = std::max(L.slot_rows, plans[m]->box_rows);
+        min_box = std::min(min_box, plans[m]->box_rows);
+    }
     const size_t slot = (size_t)L.slot_rows * plans[0]->row_bytes;
     // + the rows an MMA reads past the ring's last slot
     const size_t vstage = L.wide ? (size_t)8 * 16 * kVRow * sizeof(float2) : 0;
     const size_t fixed = 1024 + (size_t)L.gs_floats * 4 + vstage + 16 + 16 + 8 * (2 * 16 + 5) + 256 +
-                         (size_t)(kRows - L.slot_rows) * plans[0]->row_bytes;
+                         (size_t)(kRows - min_box) * plans[0]->row_bytes;
     auto fit = [&](int atoms) {
         const size_t sb = (size_t)plans[0]->planes * atoms * slot * (L.wide ? 3 : 1);
         return std::min<int>(16, (int)((kSmemBudget - fixed) / sb));

@@ -175,3 +175,28 @@ def test_batch_every_fengine_kind_with_corrections(lib, one):
     for (N, K), V, R, nm in zip(modes, vis, refs, n):
         assert nm == T // K
         assert norm_err(V, R, N) <= 1e-5, (N, K)
+
+
+# FP16 / FP8 with the four modes (N = 256 as work groups beside the
+# single-block modes in one launch; 128, 32, 16 and 64 frames): about twice
+# the errors measured on a GB300 (FP16 1.9e-4, 3.8e-4, 5.1e-4, 3.0e-4; FP8
+# 2.5e-2, 4.3e-2, 6.3e-2, 3.6e-2 -- FP8's error falls as 1/sqrt(frames))
+MIXED_BOUND = {("fp16", 512): 3.9e-4, ("fp16", 2048): 7.6e-4, ("fp16", 4096): 1.03e-3,
+               ("fp16", 1024): 6.0e-4, ("fp8", 512): 5.0e-2, ("fp8", 2048): 8.6e-2,
+               ("fp8", 4096): 1.27e-1, ("fp8", 1024): 7.2e-2}
+
+
+@pytest.mark.parametrize("one", [False, True])
+@pytest.mark.parametrize("dtype", ["fp16", "fp8"])
+def test_batch_reduced_precision_with_a_multiblock_mode(lib, dtype, one):
+    from conftest import report_err
+    modes = MODES4
+    T = 1 << 16
+    dev, refs = make_inputs(modes, T, seed=11020148 + 48)
+    with lib.CorrelatorBatch(modes, dtype, one_launch=one) as b:
+        b.push(dev)
+        vis, n = b.dump(fp64=True)
+    for (N, K), V, R, nm in zip(modes, vis, refs, n):
+        assert nm == T // K
+        e = report_err(f"batch4-{dtype}-N{N}-K{K}-one{int(one)}", norm_err(V, R, N))
+        assert e <= MIXED_BOUND[(dtype, K)], (N, K, e)

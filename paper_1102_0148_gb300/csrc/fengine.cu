@@ -461,6 +461,15 @@ __device__ __forceinline__ void frad16_block(const FengineArgs& a, int i, int64_
         tw1[e] = a.twiddle[(2 * tt * kk) & (2 * L - 1)];
     }
     for (int e = tid; e < 16 * R; e += kRadThreads) tw2[e] = a.twiddle[32 * (e >> 4) * (e & 15)];
+    // The split's W_K^k for k = t + B m is W_K^t (a register) times
+    // W_K^{B m} = W32^m (an immediate), and the antenna's pre-cast scales of
+    // the thread's 16 outputs are read once for both rounds: no global load
+    // per output.
+    const float2 wkt = __ldg(a.twiddle + t);
+    float scl[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m)
+        scl[m] = (OUT == SPEC_F16 || OUT == SPEC_F8) ? __ldg(a.scale + (int64_t)i * L + t + B * m) : 1.0f;
 
     uint4 raw0 = make_uint4(0u, 0u, 0u, 0u), raw1 = raw0;
     {
@@ -519,11 +528,11 @@ __device__ __forceinline__ void frad16_block(const FengineArgs& a, int i, int64_
 #pragma unroll
             for (int k3 = 0; k3 < R; ++k3) xb[k1 + 16 * (r * Q + qq) + 256 * k3] = x[qq * R + k3];
         group_bar(bar, B);
-#pragma unroll 4
+#pragma unroll
         for (int m = 0; m < 16; ++m) {
             const int k = t + B * m;
             const float2 zk = xb[k], zc = xb[(L - k) & (L - 1)];
-            const float2 w = __ldg(a.twiddle + k);
+            const float2 w = w32mul(wkt, m);                    // W_K^k
             const float2 wp = make_float2(0.5f * post * w.y, -0.5f * post * w.x);
             const float2 S = make_float2(zk.x + zc.x, zk.y - zc.y);
             const float2 D = make_float2(zk.x - zc.x, zk.y + zc.y);
@@ -534,9 +543,8 @@ __device__ __forceinline__ void frad16_block(const FengineArgs& a, int i, int64_
                 if (s < a.S) a.debug_out[((int64_t)i * a.S + s) * L + k] = X;
             } else {
                 if (OUT == SPEC_F16 || OUT == SPEC_F8) {
-                    const float sc = __ldg(a.scale + (int64_t)i * L + k);
-                    X.x *= sc;
-                    X.y *= sc;
+                    X.x *= scl[m];
+                    X.y *= scl[m];
                 }
                 stg[f * SR + k] = X.x;
                 stg[f * SR + L + k] = X.y;

@@ -204,6 +204,10 @@ constexpr int kX1024Stride = 33;     // exchange row stride (complex)
 // so three CTAs fit on an SM.
 constexpr int kStg1024Row = 1058;
 constexpr int kStg1024Floats = kF1024Frames * kStg1024Row;
+// Offset of the imaginary parts in a staging row: 516 = 4 mod 32 puts a
+// channel's Re and Im of one frame on banks 4 apart, so the store phase's
+// reads of (4 channels x Re/Im x 4 frame quads) hit 32 distinct banks.
+constexpr int kIm1024 = 516;
 static_assert(kStg1024Row % 8 == 2 && kStg1024Row >= 16 * kX1024Stride * 2 + 2, "staging row layout");
 
 // The body: 16 frames from s0 of antenna i by kF1024Threads threads (tid),
@@ -315,7 +319,7 @@ __device__ __forceinline__ void f1024_block(const FengineArgs& a, int i, int64_t
                     X.y *= sc;
                 }
                 stg[f * kStg1024Row + k] = X.x;
-                stg[f * kStg1024Row + 512 + k] = X.y;
+                stg[f * kStg1024Row + kIm1024 + k] = X.y;
             }
         };
 #pragma unroll
@@ -343,13 +347,16 @@ __device__ __forceinline__ void f1024_block(const FengineArgs& a, int i, int64_t
     }
     if (DEBUG) return;
     sync();
-    // 1024 workspace rows (plane, k) x 16 frames: 4 lanes per row, 4 frames each
-    const int m = lane & 3;
-    for (int row = 8 * warp + (lane >> 2); row < 1024; row += 8 * (kF1024Threads / 32)) {
-        const int plane = row >> 9;
-        const int k = row & 511;
-        const float* src = stg + 4 * m * kStg1024Row + row;
-        const int64_t off = spec_off(k, spec_row(plane, i, a.N), a.s_base + s0 + 4 * m, a.N,
+    // 512 channels x (Re, Im) x 16 frames: lane = 8 c + 4 p + m writes frames
+    // 4m .. 4m + 3 of plane p of channel 4 (warp + 8 j) + c.  The Re and Im
+    // rows of a channel are adjacent in the workspace (rows 2i, 2i + 1), so
+    // one warp store covers 4 channels' pairs of rows: 4 lines where the
+    // (plane, channel)-major order touched 8.
+    const int m = lane & 3, p = (lane >> 2) & 1, c = lane >> 3;
+    for (int cg = warp; cg < 128; cg += kF1024Threads / 32) {
+        const int k = 4 * cg + c;
+        const float* src = stg + 4 * m * kStg1024Row + p * kIm1024 + k;
+        const int64_t off = spec_off(k, spec_row(p, i, a.N), a.s_base + s0 + 4 * m, a.N,
                                      a.K >> 1, spec_tile_shift(OUT));
         store4<OUT>(a.spec, off, a.plane_stride, src[0], src[kStg1024Row], src[2 * kStg1024Row],
                     src[3 * kStg1024Row]);
@@ -426,7 +433,11 @@ struct Rad16Shape {
     static constexpr int G = kRadThreads / B;         // spectra in flight per CTA
     static constexpr int FT = 2 * G;                  // frames per CTA
     static constexpr int M = FT / 4;                  // lanes per row in the store
-    static constexpr int SR = 2 * L + 8 / M;          // staging row stride (floats)
+    // staging row: Re at 0, Im at IM; SR = 2 mod 32 (M = 4) or 4 mod 32
+    // (M = 2) and IM = 4 or 8 mod 32 put the store phase's reads of
+    // (channels x Re/Im x frame groups) on 32 distinct banks
+    static constexpr int IM = L + 16 / M;
+    static constexpr int SR = 2 * L + 32 + 8 / M;     // staging row stride (floats)
     static constexpr int STG = (FT * SR + 3) & ~3;    // staging floats
     static constexpr int XB = 272 * R;                // exchange complex per group
     static size_t smem(bool dbg) {
@@ -444,7 +455,7 @@ __device__ __forceinline__ void frad16_block(const FengineArgs& a, int i, int64_
     constexpr bool DEBUG = OUT == kOutDebug;
     using Sh = Rad16Shape<R>;
     constexpr int L = Sh::L, B = Sh::B, Q = Sh::Q, G = Sh::G, M = Sh::M, SR = Sh::SR,
-                  XB = Sh::XB;
+                  XB = Sh::XB, IM = Sh::IM;
     float* stg = reinterpret_cast<float*>(smem);                                // [FT][SR]
     float2* xbuf = reinterpret_cast<float2*>(stg + (DEBUG ? 0 : Sh::STG));      // [G][XB]
     float2* tw1 = xbuf + G * XB;                                                // [16 k1][B t]
@@ -547,22 +558,25 @@ __device__ __forceinline__ void frad16_block(const FengineArgs& a, int i, int64_
                     X.y *= scl[m];
                 }
                 stg[f * SR + k] = X.x;
-                stg[f * SR + L + k] = X.y;
+                stg[f * SR + IM + k] = X.y;
             }
         }
         group_bar(bar, B);
     }
     if (DEBUG) return;
     sync();
-    // 2L workspace rows (plane, k) x FT frames: M lanes per row, 4 frames each
+    // L channels x (Re, Im) x FT frames: lane = (2 c + p) M + m writes frames
+    // 4m .. 4m + 3 of plane p of channel CPW cg + c; a channel's Re and Im
+    // rows are adjacent in the workspace, so a warp store covers CPW lines
+    // where the (plane, channel)-major order touched 2 CPW
     const int l32 = tid & 31, warp = tid >> 5;
-    const int m = l32 % M;
-    constexpr int RPW = 32 / M;
+    const int m = l32 % M, p = (l32 / M) & 1, c = l32 / (2 * M);
+    constexpr int CPW = 32 / (2 * M);
     if (s0 + 4 * m >= a.S_pad) return;
-    for (int row = RPW * warp + l32 / M; row < 2 * L; row += RPW * (kRadThreads / 32)) {
-        const int plane = row / L;
-        const int k = row - plane * L;
-        const float* src = stg + 4 * m * SR + row;
+    for (int cg = warp; cg < L / CPW; cg += kRadThreads / 32) {
+        const int k = CPW * cg + c;
+        const int plane = p;
+        const float* src = stg + 4 * m * SR + p * IM + k;
         const int64_t off = spec_off(k, spec_row(plane, i, a.N), a.s_base + s0 + 4 * m, a.N,
                                      a.K >> 1, spec_tile_shift(OUT));
         store4<OUT>(a.spec, off, a.plane_stride, src[0], src[SR], src[2 * SR], src[3 * SR]);

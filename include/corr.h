@@ -113,7 +113,8 @@ int corr_set_chunk(corr_t h, int64_t max_spectra);
 /* Tile choices of the tensor-core X-engine (no counterpart in the paper; the
  * autotuner in paper_1102_0148_gb300/tune.py picks them): `window` = spectra
  * accumulated in TMEM before the epilogue adds them up in FP32 (a multiple
- * of 32, of 128 for FP8; 0 = 256 in FP32 mode, 512 for FP16 / FP8), `stages` = depth of the shared-memory
+ * of 32, of 128 for FP8; 0 = 256 in FP32 mode, 512 for FP16
+ * (1024 above 64 antennas), 2048 for FP8), `stages` = depth of the shared-memory
  * operand ring (2..16, clipped to what shared memory holds; 0 = automatic),
  * `split` = ranges of spectra per channel and antenna-block pair into which
  * a pass is cut (1..64, partials combined in a fixed order inside the

@@ -1044,11 +1044,13 @@ LaunchShape launch_shape(TcPlan* const* plans, int n) {
     L.stages = plans[0]->stages ? std::min(plans[0]->stages, smax) : std::min(smax, 8);
     const int step = plans[0]->KT * L.atoms;
     // default window: 256 spectra in FP32 mode (TMEM accumulation bias ~1e-6
-    // at full size); 512 for FP16 / FP8 (their input rounding dominates),
-    // 1024 when a mode has several antenna blocks (~10% less time per pass
-    // at N = 256; at N = 44 it raised the 1 s FP16 error from 5.7e-6 to
-    // 8.1e-6 for no gain)
-    const int W0 = plans[0]->mode == 0 ? 256 : (L.wide ? 1024 : 512);
+    // at full size); 512 for FP16 (its input rounding dominates), 1024 when
+    // a mode has several antenna blocks (~10% less time per pass at N = 256;
+    // at N = 44 it raised the 1 s FP16 error from 5.7e-6 to 8.1e-6 for no
+    // gain); 2048 for FP8 (16 k-tiles of 128 spectra, the MMA steps of a
+    // 1024-spectrum FP16 window: 30% less time per pass than 1024 at
+    // N = 256, 13% at N = 44, against an input rounding error near 1e-2)
+    const int W0 = plans[0]->mode == 0 ? 256 : plans[0]->mode == 2 ? 2048 : (L.wide ? 1024 : 512);
     int W = plans[0]->window ? plans[0]->window : std::max(W0, plans[0]->KT);
     L.W = (W + step - 1) / step * step;   // windows hold whole stages
     L.smem = fixed + (size_t)L.stages * stage_bytes;

@@ -23,7 +23,7 @@ import json
 import os
 
 WINDOWS = {"fp32": (64, 128, 256), "fp16": (128, 256, 512, 1024, 2048),
-           "fp8": (128, 256, 512, 1024, 2048)}
+           "fp8": (256, 512, 1024, 2048, 4096)}
 STAGES = (2, 3, 4, 6, 8)
 CHUNKS = (1024, 2048, 4096)
 SPLITS = (0, 1, 2, 4)

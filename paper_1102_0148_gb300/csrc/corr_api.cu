@@ -102,6 +102,11 @@ struct corr_s {
     void* vis_dev = nullptr;
     int64_t n_spec = 0;
     bool acc_zero = true;        // acc holds zeros (created, or dumped since its last pass)
+    // partial slot 0 holds the integration so far, the pass result of a
+    // multi-block mode that went into a zero accumulator, and acc still holds
+    // zeros: a dump reads the slot directly, anything else that needs acc or
+    // the partials first reduces it into acc (settle_partial)
+    bool part_pending = false;
     int64_t fill = 0;            // frames waiting in the workspace for the X-engine
     double2* fill_acc = nullptr; // accumulator those frames belong to
     TcPlan* tc = nullptr;
@@ -360,13 +365,34 @@ int fengine_pass(corr_t h, const uint8_t* din, int64_t S, bool raw, int64_t off)
     return CORR_OK;
 }
 
+// A pass result left in partial slot 0 goes into the (zero) accumulator
+// before the next launch that writes the partials or uses acc.
+int settle_partial(corr_t h) {
+    if (!h->part_pending) return CORR_OK;
+    h->part_pending = false;
+    h->acc_zero = false;
+    prof_begin(h);
+    CUDA_TRY(h, launch_reduce_partials(h->partial, 1, (int64_t)h->C * h->P, h->acc, h->stream,
+                                       true));
+    prof_end(h, CORR_KERNEL_REDUCE);
+    return CORR_OK;
+}
+
 // FP64 reduction of a tensor-core launch's partials, when it wrote any.
 int finish_tc_run(corr_t h, const TcRun& run, double2* acc) {
-    // a multi-block mode's pass result covers every (k, p): into a zero
-    // accumulator it is stored, not added
+    if (run.direct) {           // single-block modes added into acc themselves
+        if (acc == h->acc) h->acc_zero = false;
+        return CORR_OK;
+    }
+    // a multi-block mode's pass result covers every (k, p) in slot 0: the
+    // first pass of an integration stays there until a dump reads it or
+    // settle_partial stores it; later passes are added
+    if (acc == h->acc && h->acc_zero && run.n_split == 1) {
+        h->part_pending = true;
+        return CORR_OK;
+    }
     const bool assign = acc == h->acc && h->acc_zero;
     if (acc == h->acc) h->acc_zero = false;
-    if (run.direct) return CORR_OK;
     prof_begin(h);
     CUDA_TRY(h, launch_reduce_partials(h->partial, run.n_split, (int64_t)h->C * h->P, acc,
                                        h->stream, assign));
@@ -376,6 +402,8 @@ int finish_tc_run(corr_t h, const TcRun& run, double2* acc) {
 
 // X-engine half of a pass over the S_pad frames in the workspace -> `acc`.
 int xengine_pass(corr_t h, int64_t S_pad, double2* acc) {
+    int src = settle_partial(h);         // the launch overwrites the partials
+    if (src != CORR_OK) return src;
     if (h->use_tc) {
         prof_begin(h);
         TcRun run{};
@@ -417,6 +445,8 @@ int xengine_pass(corr_t h, int64_t S_pad, double2* acc) {
 // The fused launch over the device-input pushes waiting for it.
 int fx_flush(corr_t h) {
     if (h->fx_pending.empty()) return CORR_OK;
+    int src = settle_partial(h);         // the fused kernel adds into acc
+    if (src != CORR_OK) return src;
     prof_begin(h);
     int rc = fx_launch(h->fx, h->fx_pending.data(), (int)h->fx_pending.size(), h->twiddle,
                        split_table(h, false), h->corr_on ? h->corr_tab : nullptr, h->acc, h->status,
@@ -909,6 +939,7 @@ int corr_state_bytes(corr_t h, size_t* bytes) {
 int corr_save_state(corr_t h, void* buf) {
     if (!h || !buf) return CORR_EINVAL;
     int frc = flush(h);
+    if (frc == CORR_OK) frc = settle_partial(h);
     if (frc != CORR_OK) return frc;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     int rc = check_status(h);
@@ -949,6 +980,7 @@ int corr_load_state(corr_t h, const void* buf) {
     const unsigned char* p = static_cast<const unsigned char*>(buf) + sizeof hd;
     const size_t ab = (size_t)h->C * h->P * sizeof(double2);
     h->acc_zero = false;
+    h->part_pending = false;
     CUDA_TRY(h, cudaMemcpy(h->acc, p, ab, cudaMemcpyHostToDevice));
     p += ab;
     if (narrow(h)) {
@@ -1144,6 +1176,28 @@ int corr_grad(corr_t h, const uint8_t* samples, int64_t n, const float* gains,
 
 namespace {
 
+// The dump kernels of the integration on stream st: the next integration's
+// scales from this one's autocorrelations (when `scales`), then vis[p][k],
+// from the accumulator (which is then cleared) or from a pass result still
+// in partial slot 0 (the accumulator is zero already).
+cudaError_t dump_ops(corr_t h, void* vis, int vis_fp64, bool scales, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (h->part_pending) {
+        if (scales)
+            e = launch_scales_from_partial(h->partial, h->N, h->C, h->P, h->n_spec,
+                                           h->scale_target, h->scale, st);
+        if (e == cudaSuccess) e = launch_dump_partial(h->partial, h->C, h->P, vis, vis_fp64, st);
+        h->part_pending = false;
+    } else {
+        if (scales)
+            e = launch_scales_from_autos(h->acc, h->N, h->C, h->P, h->n_spec, h->scale_target,
+                                         h->scale, st);
+        if (e == cudaSuccess) e = launch_dump(h->acc, h->C, h->P, vis, vis_fp64, st);
+    }
+    h->acc_zero = true;
+    return e;
+}
+
 // Queue the dump of the integration into `vis` on the handle's stream.
 int enqueue_dump(corr_t h, void* vis, int vis_fp64, bool dev) {
     int frc = flush(h);
@@ -1154,15 +1208,11 @@ int enqueue_dump(corr_t h, void* vis, int vis_fp64, bool dev) {
         if (!h->vis_dev) CUDA_TRY(h, dev_malloc(&h->vis_dev, (size_t)h->C * h->P * sizeof(double2)));
         out = h->vis_dev;
     }
-    if (narrow(h) && !h->scales_user && h->n_spec > 0) {
-        // the next integration is scaled from this one's autocorrelations
-        CUDA_TRY(h, launch_scales_from_autos(h->acc, h->N, h->C, h->P, h->n_spec, h->scale_target,
-                                             h->scale, h->stream));
-        h->scales_ready = true;
-    }
+    // the next integration is scaled from this one's autocorrelations
+    const bool scales = narrow(h) && !h->scales_user && h->n_spec > 0;
     prof_begin(h);
-    CUDA_TRY(h, launch_dump(h->acc, h->C, h->P, out, vis_fp64, h->stream));   // also clears acc
-    h->acc_zero = true;
+    CUDA_TRY(h, dump_ops(h, out, vis_fp64, scales, h->stream));
+    if (scales) h->scales_ready = true;
     prof_end(h, CORR_KERNEL_DUMP);
     if (!dev) CUDA_TRY(h, cudaMemcpyAsync(vis, out, bytes, cudaMemcpyDeviceToHost, h->stream));
     return CORR_OK;
@@ -1419,7 +1469,11 @@ int batch_enqueue(corr_batch_t b, const uint8_t* const* samples, const int64_t* 
                 if (rc != CORR_OK) return batch_from_handle(b, idx[a], rc);
             }
         }
-        // one tensor-core launch over all of them
+        // one tensor-core launch over all of them (it overwrites their partials)
+        for (int a = 0; a < na; ++a) {
+            int src = settle_partial(b->h[idx[a]]);
+            if (src != CORR_OK) return batch_from_handle(b, idx[a], src);
+        }
         prof_begin(h0);
         int rc = tc_launch(plans, na, runs, b->stream, b->err);
         if (rc != CORR_OK) return rc;
@@ -1546,11 +1600,7 @@ int corr_batch_capture(corr_batch_t b, const uint8_t* const* samples, const int6
         rc = batch_enqueue(b, samples, n);
         for (int m = 0; rc == CORR_OK && m < b->n; ++m) {
             corr_t h = b->h[m];
-            if (narrow(h) && !h->scales_user)
-                e = launch_scales_from_autos(h->acc, h->N, h->C, h->P, h->n_spec, h->scale_target,
-                                             h->scale, b->stream);
-            if (e == cudaSuccess) e = launch_dump(h->acc, h->C, h->P, vis[m], vis_fp64, b->stream);
-            h->acc_zero = true;
+            e = dump_ops(h, vis[m], vis_fp64, narrow(h) && !h->scales_user, b->stream);
             if (e != cudaSuccess) rc = CORR_ECUDA;
         }
         cudaGraph_t g = nullptr;

@@ -144,13 +144,20 @@ cudaError_t launch_reduce_partials(const float2* partial, int n_split, int64_t C
 
 // vis[p][k] = acc[k][p] as complex64 (fp64 == 0) or complex128; then acc = 0.
 cudaError_t launch_dump(double2* acc, int C, int P, void* vis, int fp64, cudaStream_t st);
+// The same from a pass result still in partial slot 0 (part[k][p], FP32),
+// with the accumulator already zero: nothing is cleared.
+cudaError_t launch_dump_partial(const float2* part, int C, int P, void* vis, int fp64,
+                                cudaStream_t st);
 
 // Pre-cast scales s[i][k] = target / sqrt(P/2) from spectra Y[N][S][C] or from
-// the autocorrelations of the FP64 accumulator acc[C][P] over n_spec spectra.
+// the autocorrelations of the FP64 accumulator acc[C][P] (or of a pass result
+// in partial slot 0) over n_spec spectra.
 cudaError_t launch_scales_from_spectra(const float2* Y, int N, int64_t S, int C, float target,
                                        float* scale, cudaStream_t st);
 cudaError_t launch_scales_from_autos(const double2* acc, int N, int C, int P, int64_t n_spec,
                                      float target, float* scale, cudaStream_t st);
+cudaError_t launch_scales_from_partial(const float2* part, int N, int C, int P, int64_t n_spec,
+                                       float target, float* scale, cudaStream_t st);
 
 // Gradient of a real loss of V with respect to the gains and delays, from the
 // uncorrected visibilities R ([C][P] FP64) and G = dL/dRe V + i dL/dIm V

@@ -38,7 +38,9 @@ __global__ void scales_from_spectra_kernel(const float2* Y, int N, int64_t S, in
     }
 }
 
-__global__ void scales_from_autos_kernel(const double2* acc, int N, int C, int P, int64_t n_spec,
+// acc: the FP64 accumulator, or (float2) a pass result still in partial slot 0
+template <typename T>
+__global__ void scales_from_autos_kernel(const T* acc, int N, int C, int P, int64_t n_spec,
                                          float target, float* scale) {
     const int64_t total = (int64_t)N * C;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -46,7 +48,7 @@ __global__ void scales_from_autos_kernel(const double2* acc, int N, int C, int P
         const int i = (int)(e / C);
         const int k = (int)(e - (int64_t)i * C);
         const int p = i * N - i * (i - 1) / 2;      // pair (i, i)
-        scale[e] = scale_for(acc[(int64_t)k * P + p].x / (double)n_spec, target);
+        scale[e] = scale_for((double)acc[(int64_t)k * P + p].x / (double)n_spec, target);
     }
 }
 
@@ -65,8 +67,15 @@ cudaError_t launch_scales_from_spectra(const float2* Y, int N, int64_t S, int C,
 
 cudaError_t launch_scales_from_autos(const double2* acc, int N, int C, int P, int64_t n_spec,
                                      float target, float* scale, cudaStream_t st) {
-    scales_from_autos_kernel<<<blocks_for((int64_t)N * C), 256, 0, st>>>(acc, N, C, P, n_spec,
-                                                                          target, scale);
+    scales_from_autos_kernel<double2><<<blocks_for((int64_t)N * C), 256, 0, st>>>(
+        acc, N, C, P, n_spec, target, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scales_from_partial(const float2* part, int N, int C, int P, int64_t n_spec,
+                                       float target, float* scale, cudaStream_t st) {
+    scales_from_autos_kernel<float2><<<blocks_for((int64_t)N * C), 256, 0, st>>>(
+        part, N, C, P, n_spec, target, scale);
     return cudaGetLastError();
 }
 

@@ -206,22 +206,31 @@ __global__ void reduce_partials_kernel(const float2* part, int n_split, int64_t 
 // acc [C][P] -> vis [P][C] through 32 x 32 shared-memory tiles, so both the
 // reads (along p) and the writes (along k) are coalesced.  (acc is cleared by
 // a memset after it: zero stores here, to the lines just loaded, held the
-// kernel to a quarter of the HBM bandwidth.)
+// kernel to a quarter of the HBM bandwidth.)  T = double2 for the FP64
+// accumulator, float2 for a pass result still in partial slot 0 (its FP64
+// reduction into a zero accumulator would give the same values); values
+// change type only on the way out, as FP64 conversions are slow here.
 constexpr int kDT = 32;
 
-__global__ void __launch_bounds__(kDT * 8) dump_kernel(const double2* __restrict__ acc, int C,
-                                                     int P, void* __restrict__ vis, int fp64) {
-    __shared__ double2 tile[kDT][kDT + 1];
+__device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ float2 to_f2(float2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
+
+template <typename T>
+__global__ void __launch_bounds__(kDT * 8) dump_kernel(const T* __restrict__ acc, int C, int P,
+                                                     void* __restrict__ vis, int fp64) {
+    __shared__ T tile[kDT][kDT + 1];
     const int p0 = blockIdx.x * kDT;
     const int k0 = blockIdx.y * kDT;
     const int tx = threadIdx.x & (kDT - 1);
     const int ty = threadIdx.x / kDT;               // 0..7
-    double2 v[kDT / 8];
+    T v[kDT / 8];
     const int p = p0 + tx;
 #pragma unroll
     for (int q = 0; q < kDT / 8; ++q) {
         const int k = k0 + ty + 8 * q;
-        v[q] = (k < C && p < P) ? acc[(int64_t)k * P + p] : make_double2(0.0, 0.0);
+        v[q] = (k < C && p < P) ? acc[(int64_t)k * P + p] : T{};
     }
 #pragma unroll
     for (int q = 0; q < kDT / 8; ++q) tile[ty + 8 * q][tx] = v[q];
@@ -231,12 +240,12 @@ __global__ void __launch_bounds__(kDT * 8) dump_kernel(const double2* __restrict
     for (int q = 0; q < kDT / 8; ++q) {
         const int pp = p0 + ty + 8 * q;
         if (k < C && pp < P) {
-            const double2 w = tile[tx][ty + 8 * q];
+            const T w = tile[tx][ty + 8 * q];
             const int64_t e = (int64_t)pp * C + k;
             if (fp64)
-                static_cast<double2*>(vis)[e] = w;
+                static_cast<double2*>(vis)[e] = to_d2(w);
             else
-                static_cast<float2*>(vis)[e] = make_float2((float)w.x, (float)w.y);
+                static_cast<float2*>(vis)[e] = to_f2(w);
         }
     }
 }
@@ -307,10 +316,17 @@ cudaError_t launch_reduce_partials(const float2* partial, int n_split, int64_t C
 
 cudaError_t launch_dump(double2* acc, int C, int P, void* vis, int fp64, cudaStream_t st) {
     dim3 grid((unsigned)((P + kDT - 1) / kDT), (unsigned)((C + kDT - 1) / kDT));
-    dump_kernel<<<grid, kDT * 8, 0, st>>>(acc, C, P, vis, fp64);
+    dump_kernel<double2><<<grid, kDT * 8, 0, st>>>(acc, C, P, vis, fp64);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cudaMemsetAsync(acc, 0, (size_t)C * P * sizeof(double2), st);
+}
+
+cudaError_t launch_dump_partial(const float2* part, int C, int P, void* vis, int fp64,
+                                cudaStream_t st) {
+    dim3 grid((unsigned)((P + kDT - 1) / kDT), (unsigned)((C + kDT - 1) / kDT));
+    dump_kernel<float2><<<grid, kDT * 8, 0, st>>>(part, C, P, vis, fp64);
+    return cudaGetLastError();
 }
 
 }  // namespace gbcorr

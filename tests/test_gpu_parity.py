@@ -358,3 +358,68 @@ def test_dump_async_matches_dump(lib, torch_cuda):
     assert np.array_equal(pinned.numpy(), V_sync)
     R2, _ = oracle.correlate(packed[S:], N, K)
     assert vis_error(on_dev.cpu().numpy(), R2, N) <= TOL
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "fp16"])
+def test_multiblock_pass_result_every_path(lib, torch_cuda, dtype):
+    """A multi-block mode's first pass of an integration stays in the FP32
+    partial buffer until the dump reads it; every other consumer (the next
+    pass, a checkpoint, a gradient evaluation into its own buffer) first
+    stores it into the FP64 accumulator.  All of them must
+    give the one-run result: 130 antennas (three blocks), K = 64."""
+    torch = torch_cuda
+    N, K = 130, 64
+    packed, _ = synth.make_samples(N, 700 * K, K, seed=SEED + 130)
+    dev = torch.from_numpy(packed.reshape(-1)).cuda()
+    rec = N * K // 2
+    bound = TOL if dtype == "fp32" else 3e-4
+    R, _ = oracle.correlate(packed[:300], N, K)          # packed is [frame][antenna][K/2]
+    R2, _ = oracle.correlate(packed[300:], N, K)
+    with lib.Correlator(N, K, dtype) as c:
+        # one pass, dumped as complex128 and as complex64 from the partials
+        c.push(dev[: 300 * rec], 300 * K)
+        V64, n = c.dump(fp64=True)
+        assert n == 300 and vis_error(V64, R, N) <= bound
+        c.push(dev[: 300 * rec], 300 * K)
+        V32, _ = c.dump(fp64=False)
+        assert np.array_equal(V32, V64.astype(np.complex64))
+        # the pass result settled by a later pass of the same integration
+        c.push(dev[: 100 * rec], 100 * K)
+        lib.corr_sync(c.h)
+        c.push(dev[100 * rec: 300 * rec], 200 * K)
+        V, n = c.dump(fp64=True)
+        assert n == 300 and vis_error(V, R, N) <= bound
+        # the next integration (FP16: scaled from the autos of the last one)
+        c.push(dev[300 * rec:], 400 * K)
+        V, n = c.dump(fp64=True)
+        assert n == 400 and vis_error(V, R2, N) <= bound
+    # three passes of 128 frames
+    with lib.Correlator(N, K, dtype, chunk=128) as c:
+        c.push(dev[: 300 * rec], 300 * K)
+        V, n = c.dump(fp64=True)
+        assert n == 300 and vis_error(V, R, N) <= bound
+    # a checkpoint taken while the first pass is pending resumes bit-identically
+    with lib.Correlator(N, K, dtype) as c:
+        c.push(dev[: 300 * rec], 300 * K)
+        c.push(dev[300 * rec:], 400 * K)
+        V_one, _ = c.dump(fp64=True)
+    with lib.Correlator(N, K, dtype) as c:
+        c.push(dev[: 300 * rec], 300 * K)
+        state = lib.corr_save_state(c.h)
+    with lib.Correlator(N, K, dtype) as c:
+        lib.corr_load_state(c.h, state)
+        c.push(dev[300 * rec:], 400 * K)
+        V_two, n = c.dump(fp64=True)
+    assert n == 700 and np.array_equal(V_one, V_two)
+    # so does a gradient evaluation between the two pushes (its own buffer)
+    if dtype == "fp32":
+        with lib.Correlator(N, K, dtype) as c:
+            c.push(dev[: 300 * rec], 300 * K)
+            gV = np.ones((c.P, c.C), np.complex128)
+            gg = np.empty(N, np.complex64)
+            gt = np.empty(N, np.float32)
+            lib.corr_grad(c.h, dev[300 * rec:], 400 * K, np.ones(N, np.complex64),
+                          np.zeros(N, np.float32), gV, True, gg, gt)
+            c.push(dev[300 * rec:], 400 * K)
+            V_three, n = c.dump(fp64=True)
+        assert n == 700 and np.array_equal(V_one, V_three)

@@ -50,9 +50,9 @@ PAPER_RATE = N_ANT * RATE
 # (summaries under profiles/); scaled to the average launch below.  Remove an
 # entry when its kernel changes.
 NCU_TRAFFIC = {
-    ("fengine", "fp32"): (145.64e6, 2048,
+    ("fengine", "fp32"): (145.59e6, 2048,
                           "ncu --set full, fengine_k512<SPEC_F16X2, corrections off>, one "
-                          "2048-frame launch: 23.10 MB read + 122.54 MB written "
+                          "2048-frame launch: 23.09 MB read + 122.49 MB written "
                           "(profiles/fengine_k512_n44_2048frames_fp32.txt)"),
 }
 
@@ -61,7 +61,7 @@ NCU_TRAFFIC = {
 # (sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed, summary
 # under profiles/).  Remove an entry when its kernel changes.
 NCU_XENGINE_TENSOR_PCT = {
-    "fp32": 35.06,   # profiles/xengine_tc_n44_k512_onepass_fp32.txt
+    "fp32": 36.38,   # profiles/xengine_tc_n44_k512_onepass_fp32.txt
 }
 
 WORKLOAD = ("N=44 antennas, K=512-point real FFT -> 256 channels, 990 outputs/channel, "

@@ -290,7 +290,8 @@ __device__ __forceinline__ void f1024_block(const FengineArgs& a, int i, int64_t
         __syncwarp();
         // radix 2 across the half-warps: half 0 forms B_t' + B_t'+16, half 1
         // W32^{t'} (B_t' - B_t'+16).  Both halves run the same instructions,
-        // y + sgn x times a twiddle row that is all ones for half 0.
+        // y + sgn x (one packed FMA) times a twiddle row that is all ones for
+        // half 0.
         const float sgn = hh ? -1.0f : 1.0f;
         const float2* twh = tw32 + 16 * hh;
 #pragma unroll
@@ -298,7 +299,7 @@ __device__ __forceinline__ void f1024_block(const FengineArgs& a, int i, int64_t
             float2 y;
             y.x = __shfl_xor_sync(0xffffffffu, x[t].x, 16);
             y.y = __shfl_xor_sync(0xffffffffu, x[t].y, 16);
-            const float2 v = make_float2(fmaf(sgn, x[t].x, y.x), fmaf(sgn, x[t].y, y.y));
+            const float2 v = __ffma2_rn(make_float2(sgn, sgn), x[t], y);
             x[t] = t > 0 ? cmul(v, twh[t]) : v;
         }
         dft16(x);

@@ -200,3 +200,52 @@ def test_batch_reduced_precision_with_a_multiblock_mode(lib, dtype, one):
         assert nm == T // K
         e = report_err(f"batch4-{dtype}-N{N}-K{K}-one{int(one)}", norm_err(V, R, N))
         assert e <= MIXED_BOUND[(dtype, K)], (N, K, e)
+
+
+# Full size, as bench.py times the batching workload: 2^22 samples per antenna
+# and mode, one pass per mode, the captured step replayed, with the tiles the
+# autotuner picks for it on a GB300.  The oracle computes four channels of
+# every mode (DC, the tone channel 97, a middle and the last channel) for all
+# pairs.  FP16 bounds: about twice the errors measured on a GB300 (2.6e-5,
+# 3.3e-5, 4.9e-5, 3.4e-5; FP32 1.3e-6 .. 1.9e-6 against its 1e-5 bar).
+FULL_T = 1 << 22
+FULL_TILES = {"fp16": (2048, 4, 0), "fp32": (256, 6, 1)}
+FULL_FP16_BOUND = {(44, 512): 5e-5, (22, 2048): 6.6e-5, (11, 4096): 1e-4, (256, 1024): 6.8e-5}
+
+
+@pytest.fixture(scope="module")
+def full_batch():
+    import torch
+    data, refs, chans = [], [], []
+    for m, (N, K) in enumerate(MODES4):
+        d, _ = synth.make_samples_torch(N, FULL_T, K, seed=11020148 + 60 + m, device="cuda",
+                                        tone_amp=0.5)
+        d = d.reshape(-1)
+        C = K // 2
+        ch = [0, 97, C // 2 + 3, C - 1]
+        R, S = oracle.visibilities_channels(d.cpu().numpy(), N, K, ch, frames_per_block=256)
+        assert S == FULL_T // K
+        data.append(d)
+        refs.append(R)
+        chans.append(ch)
+    return data, refs, chans
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "fp16"])
+def test_batch_full_size_sampled_channels(lib, full_batch, dtype):
+    import torch
+    data, refs, chans = full_batch
+    w, st, sp = FULL_TILES[dtype]
+    with lib.CorrelatorBatch(MODES4, dtype, window=w, stages=st, split=sp) as b:
+        for h, (N, K) in zip(b.handles, MODES4):
+            lib.corr_set_chunk(h, FULL_T // K)          # one pass per mode and push
+        vis = [torch.empty((N * (N + 1) // 2, K // 2), dtype=torch.complex64, device="cuda")
+               for N, K in MODES4]
+        b.capture(data, vis)
+        n = b.replay()
+        b.sync()
+    for (N, K), V, R, ch, nm in zip(MODES4, vis, refs, chans, n):
+        assert nm == FULL_T // K
+        e = norm_err(V.cpu().numpy()[:, ch], R, N)
+        print(f"MEASURED_ERR batchfull-{dtype}-N{N}-K{K} {e:.3e}")
+        assert e <= (1e-5 if dtype == "fp32" else FULL_FP16_BOUND[(N, K)]), (N, K, e)

@@ -166,6 +166,12 @@ constexpr int kOutDebug = -1;
 constexpr int kStgRow = 547;
 constexpr int kStgFloats = kF512Frames * kStgRow;
 static_assert(kStgRow % 32 == 3 && kStgRow >= 16 * kXStride * 2 + 3, "staging row layout");
+// Start of frame f's staging row: odd rows one float later, so every row
+// starts on an 8-byte boundary and a channel's (Re, Im) is one 8-byte store
+// (K = 512 FP32 mode 1.5% faster than two 4-byte stores).  The column reads
+// of the store phase stay on distinct banks: the offset is the same for
+// all lanes of a read.
+__device__ __forceinline__ int stg_row(int f) { return f * kStgRow + (f & 1); }
 
 // Four consecutive frames of one workspace row (channel k, row r) from the
 // staging buffer, converted and stored with one vector store per plane.
@@ -286,7 +292,7 @@ __device__ __forceinline__ void store_rows(char* base, int N, int64_t plane_stri
         for (int j = 0; j < 8; ++j) {
             float v[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = src[e * kStgRow];
+            for (int e = 0; e < 8; ++e) v[e] = src[e * kStgRow + (e & 1)];
             store8p<OUT>(dst, lo, v);
             dst += step;
             src += 64;
@@ -298,7 +304,7 @@ __device__ __forceinline__ void store_rows(char* base, int N, int64_t plane_stri
         const int64_t step = ((int64_t)16 * 2 * N << tsh) * eb;     // 16 channels on
 #pragma unroll 1
         for (int j = 0; j < 16; ++j) {
-            store4p<OUT>(dst, lo, src[0], src[kStgRow], src[2 * kStgRow], src[3 * kStgRow]);
+            store4p<OUT>(dst, lo, src[0], src[kStgRow + 1], src[2 * kStgRow], src[3 * kStgRow + 1]);
             dst += step;
             src += 32;
         }
@@ -372,7 +378,7 @@ __device__ __forceinline__ void f512_block(const F512Block& b, const float2* __r
     sync();
 
     const int fx = 2 * warp + half + 16;             // the group's second frame
-    float2* gx = reinterpret_cast<float2*>(stg + fx * kStgRow + (fx & 3));
+    float2* gx = reinterpret_cast<float2*>(stg + stg_row(fx) + ((4 - (stg_row(fx) & 3)) & 3));
     unsigned char* gbytes = reinterpret_cast<unsigned char*>(gx);
 
 #pragma unroll 1
@@ -428,8 +434,7 @@ __device__ __forceinline__ void f512_block(const F512Block& b, const float2* __r
                     X.x *= sc;
                     X.y *= sc;
                 }
-                stg[f * kStgRow + 2 * k] = X.x;
-                stg[f * kStgRow + 2 * k + 1] = X.y;
+                *reinterpret_cast<float2*>(stg + stg_row(f) + 2 * k) = X;
             }
         };
 #pragma unroll

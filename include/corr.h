@@ -180,7 +180,7 @@ int corr_push(corr_t h, const uint8_t* samples, int64_t n);
  * holding F-engine and X-engine warps, the spectra passed through a ring of
  * workspace slots that stays in L2 instead of a workspace in HBM.  Off by
  * default: on a GB300 at N = 44 the separate F- and X-engine launches are
- * faster (2.4 against 3.7 ms per 1 s integration at 35 MS/s).
+ * faster (2.35 against 3.65 ms per 1 s integration at 35 MS/s).
  * corr_set_fused(h, 1) turns it on (allocating its ~69 MB ring on the first
  * call), CORR_EUNSUPPORTED where it is not served (other K, N or dtype, or a
  * device without cooperative launches); (h, 0) turns it off.  Pushes from

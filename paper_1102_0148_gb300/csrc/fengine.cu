@@ -197,17 +197,14 @@ __global__ void __launch_bounds__(kF512Threads, 3) fengine_k512(FengineArgs a) {
 constexpr int kF1024Frames = 16;     // frames per CTA, two per warp
 constexpr int kF1024Threads = 256;
 constexpr int kX1024Stride = 33;     // exchange row stride (complex)
-// Staging row stride (floats): 1058 = 2 mod 8 keeps the store phase's column
-// reads on distinct banks, and a row holds one warp's exchange area (16 x 33
-// complex = 1056 floats) at the 16-byte aligned offset 2 (f mod 2).  A warp
-// exchanges through the row of its second frame, as in the K = 512 kernel,
-// so three CTAs fit on an SM.
+// Staging rows [frame][2 k + plane] (a channel's Re and Im side by side, one
+// 8-byte store).  Row stride (floats): 1058 = 2 mod 32 puts the store phase's
+// reads of (4 channels x Re/Im x 4 frame quads) on 32 distinct banks, and a
+// row holds one warp's exchange area (16 x 33 complex = 1056 floats) at the
+// 16-byte aligned offset 2 (f mod 2).  A warp exchanges through the row of
+// its second frame, as in the K = 512 kernel, so three CTAs fit on an SM.
 constexpr int kStg1024Row = 1058;
 constexpr int kStg1024Floats = kF1024Frames * kStg1024Row;
-// Offset of the imaginary parts in a staging row: 516 = 4 mod 32 puts a
-// channel's Re and Im of one frame on banks 4 apart, so the store phase's
-// reads of (4 channels x Re/Im x 4 frame quads) hit 32 distinct banks.
-constexpr int kIm1024 = 516;
 static_assert(kStg1024Row % 8 == 2 && kStg1024Row >= 16 * kX1024Stride * 2 + 2, "staging row layout");
 
 // The body: 16 frames from s0 of antenna i by kF1024Threads threads (tid),
@@ -319,8 +316,7 @@ __device__ __forceinline__ void f1024_block(const FengineArgs& a, int i, int64_t
                     X.x *= sc;
                     X.y *= sc;
                 }
-                stg[f * kStg1024Row + k] = X.x;
-                stg[f * kStg1024Row + kIm1024 + k] = X.y;
+                *reinterpret_cast<float2*>(stg + f * kStg1024Row + 2 * k) = X;
             }
         };
 #pragma unroll
@@ -331,8 +327,8 @@ __device__ __forceinline__ void f1024_block(const FengineArgs& a, int i, int64_t
             zc.y = __shfl_sync(0xffffffffu, x[15 - q].y, src);
             if (lane == 0) zc = x[(16 - q) & 15];
             const float2 zk = x[q];
-            const float2 S = make_float2(zk.x + zc.x, zk.y - zc.y);
-            const float2 D = make_float2(zk.x - zc.x, zk.y + zc.y);
+            const float2 S = add_conj(zk, zc);
+            const float2 D = sub_conj(zk, zc);
             // B = w'_k D = -i c W1024^l W32^q D
             const float2 v = cmul(u, w32mul(D, q));
             const float2 B = make_float2(v.y, -v.x);
@@ -356,7 +352,7 @@ __device__ __forceinline__ void f1024_block(const FengineArgs& a, int i, int64_t
     const int m = lane & 3, p = (lane >> 2) & 1, c = lane >> 3;
     for (int cg = warp; cg < 128; cg += kF1024Threads / 32) {
         const int k = 4 * cg + c;
-        const float* src = stg + 4 * m * kStg1024Row + p * kIm1024 + k;
+        const float* src = stg + 4 * m * kStg1024Row + 2 * k + p;
         const int64_t off = spec_off(k, spec_row(p, i, a.N), a.s_base + s0 + 4 * m, a.N,
                                      a.K >> 1, spec_tile_shift(OUT));
         store4<OUT>(a.spec, off, a.plane_stride, src[0], src[kStg1024Row], src[2 * kStg1024Row],

@@ -430,10 +430,9 @@ struct Rad16Shape {
     static constexpr int G = kRadThreads / B;         // spectra in flight per CTA
     static constexpr int FT = 2 * G;                  // frames per CTA
     static constexpr int M = FT / 4;                  // lanes per row in the store
-    // staging row: Re at 0, Im at IM; SR = 2 mod 32 (M = 4) or 4 mod 32
-    // (M = 2) and IM = 4 or 8 mod 32 put the store phase's reads of
-    // (channels x Re/Im x frame groups) on 32 distinct banks
-    static constexpr int IM = L + 16 / M;
+    // staging row [2 k + plane] (a channel's Re and Im side by side, one
+    // 8-byte store); SR = 2 mod 32 (M = 4) or 4 mod 32 (M = 2) puts the store
+    // phase's reads of (channels x Re/Im x frame groups) on 32 distinct banks
     static constexpr int SR = 2 * L + 32 + 8 / M;     // staging row stride (floats)
     static constexpr int STG = (FT * SR + 3) & ~3;    // staging floats
     static constexpr int XB = 272 * R;                // exchange complex per group
@@ -452,7 +451,7 @@ __device__ __forceinline__ void frad16_block(const FengineArgs& a, int i, int64_
     constexpr bool DEBUG = OUT == kOutDebug;
     using Sh = Rad16Shape<R>;
     constexpr int L = Sh::L, B = Sh::B, Q = Sh::Q, G = Sh::G, M = Sh::M, SR = Sh::SR,
-                  XB = Sh::XB, IM = Sh::IM;
+                  XB = Sh::XB;
     float* stg = reinterpret_cast<float*>(smem);                                // [FT][SR]
     float2* xbuf = reinterpret_cast<float2*>(stg + (DEBUG ? 0 : Sh::STG));      // [G][XB]
     float2* tw1 = xbuf + G * XB;                                                // [16 k1][B t]
@@ -542,8 +541,8 @@ __device__ __forceinline__ void frad16_block(const FengineArgs& a, int i, int64_
             const float2 zk = xb[k], zc = xb[(L - k) & (L - 1)];
             const float2 w = w32mul(wkt, m);                    // W_K^k
             const float2 wp = make_float2(0.5f * post * w.y, -0.5f * post * w.x);
-            const float2 S = make_float2(zk.x + zc.x, zk.y - zc.y);
-            const float2 D = make_float2(zk.x - zc.x, zk.y + zc.y);
+            const float2 S = add_conj(zk, zc);
+            const float2 D = sub_conj(zk, zc);
             const float2 wd = cmul(wp, D);
             float2 X = make_float2(fmaf(chalf, S.x, wd.x), fmaf(chalf, S.y, wd.y));
             if (a.corr) X = cmul(__ldg(a.corr + (int64_t)i * L + k), X);
@@ -554,8 +553,7 @@ __device__ __forceinline__ void frad16_block(const FengineArgs& a, int i, int64_
                     X.x *= scl[m];
                     X.y *= scl[m];
                 }
-                stg[f * SR + k] = X.x;
-                stg[f * SR + IM + k] = X.y;
+                *reinterpret_cast<float2*>(stg + f * SR + 2 * k) = X;
             }
         }
         group_bar(bar, B);
@@ -573,7 +571,7 @@ __device__ __forceinline__ void frad16_block(const FengineArgs& a, int i, int64_
     for (int cg = warp; cg < L / CPW; cg += kRadThreads / 32) {
         const int k = CPW * cg + c;
         const int plane = p;
-        const float* src = stg + 4 * m * SR + p * IM + k;
+        const float* src = stg + 4 * m * SR + 2 * k + p;
         const int64_t off = spec_off(k, spec_row(plane, i, a.N), a.s_base + s0 + 4 * m, a.N,
                                      a.K >> 1, spec_tile_shift(OUT));
         store4<OUT>(a.spec, off, a.plane_stride, src[0], src[SR], src[2 * SR], src[3 * SR]);
